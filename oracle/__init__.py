@@ -1,0 +1,228 @@
+"""CPU oracle for the anisotropic-diffusion hot path (arXiv:1609.03782, Sec. 3.3).
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, obviously correct
+statement of what the GPU library computes: double precision, single thread,
+no blocking or fusion beyond what the paper's definitions state.  Only
+``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of
+``bench.py`` may import it.  It shares no code with the CUDA library
+(``paper_1609_03782_gb300``) and never imports it; the library never imports
+this package.
+
+Parity pins: every function here is checked in ``tests/test_oracle_pins.py``
+against hand-worked values, closed forms, invariants or library routines.
+
+Contents
+--------
+pm_filter            per-face Perona-Malik iteration (Sec. 3.3, eq. "perona" and
+                     the gradient conductance printed after it), C code in
+                     ``afd_oracle.c``
+pm_filter_box        the same, evaluated for one sub-box only through the
+                     domain of dependence of an explicit n-step stencil
+intensity_filter     the paper's intensity-driven update (Sec. 3.3, eq. after
+                     "conductivepara")
+stats / noise_rms    FP64 sums and the negative-half noise estimate (K is set
+                     in units of the noise level, Sec. 3.3)
+quantize/dequantize  2-byte storage formats with a power-of-two per-cube scale
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "afd_oracle.c")
+_LIB = os.path.join(_HERE, "liborcafd.so")
+_lock = threading.Lock()
+_lib = None
+
+COND_EXPONENTIAL = 0
+COND_RATIONAL = 1
+_COND = {"exponential": COND_EXPONENTIAL, "rational": COND_RATIONAL}
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (plain -O2, no FP contraction)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def load_library(path: str):
+    """Load an oracle shared object and declare its signatures."""
+    lib = ctypes.CDLL(path)
+    i64, dbl, c_int = ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    vp = ctypes.c_void_p
+    lib.orc_pm_filter.argtypes = [vp, i64, i64, i64, dbl, dbl, dbl,
+                                  dbl, dbl, c_int, c_int]
+    lib.orc_pm_filter.restype = c_int
+    lib.orc_intensity_filter.argtypes = [vp, i64, i64, i64, dbl, dbl,
+                                         dbl, dbl, dbl, dbl, c_int]
+    lib.orc_intensity_filter.restype = c_int
+    lib.orc_stats.argtypes = [vp, i64, vp]
+    lib.orc_stats.restype = None
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = load_library(build())
+    return _lib
+
+
+def _shape3(a: np.ndarray):
+    if a.ndim != 3:
+        raise ValueError("cube must be 3-D, shaped (nz, ny, nx)")
+    nz, ny, nx = a.shape
+    return nx, ny, nz
+
+
+def pm_filter(cube, K: float, dt: float, n_iter: int,
+              conductance: str = "rational", spacing=(1.0, 1.0, 1.0),
+              lib=None) -> np.ndarray:
+    """n_iter per-face Perona-Malik iterations in FP64; returns a new array.
+
+    ``cube`` is shaped (nz, ny, nx) (x fastest); it is converted to float64.
+    ``spacing`` is (hx, hy, hz).  K is in absolute intensity units.  ``lib``
+    selects another build of ``afd_oracle.c`` (the mutation tests use it).
+    """
+    a = np.ascontiguousarray(cube, dtype=np.float64).copy()
+    nx, ny, nz = _shape3(a)
+    hx, hy, hz = (float(s) for s in spacing)
+    rc = (lib or _load()).orc_pm_filter(a.ctypes.data, nx, ny, nz, hx, hy, hz,
+                               float(K), float(dt), int(n_iter),
+                               _COND[conductance])
+    if rc != 0:
+        raise ValueError("oracle pm_filter rejected its arguments")
+    return a
+
+
+def pm_filter_box(cube, box, K: float, dt: float, n_iter: int,
+                  conductance: str = "rational",
+                  spacing=(1.0, 1.0, 1.0)) -> np.ndarray:
+    """Oracle result for the sub-box ``box`` = ((z0,z1),(y0,y1),(x0,x1)) only.
+
+    An explicit nearest-neighbour iteration moves information one voxel per
+    step, so after n_iter steps a voxel depends only on voxels within n_iter
+    of it along each axis.  The box is grown by n_iter on every side (clamped
+    to the cube, where the true zero-flux faces then apply), filtered there,
+    and the centre cut out.  Within the box the result is the full-cube
+    oracle's, operation for operation.
+    """
+    (z0, z1), (y0, y1), (x0, x1) = box
+    nz, ny, nx = cube.shape
+    g = int(n_iter)
+    gz0, gz1 = max(0, z0 - g), min(nz, z1 + g)
+    gy0, gy1 = max(0, y0 - g), min(ny, y1 + g)
+    gx0, gx1 = max(0, x0 - g), min(nx, x1 + g)
+    sub = cube[gz0:gz1, gy0:gy1, gx0:gx1]
+    out = pm_filter(sub, K, dt, n_iter, conductance, spacing)
+    return out[z0 - gz0:z1 - gz0, y0 - gy0:y1 - gy0, x0 - gx0:x1 - gx0].copy()
+
+
+def intensity_filter(cube, K: float, rms: float, tau: float, n_iter: int,
+                     C=(5.0, 5.0, 5.0)) -> np.ndarray:
+    """The paper's intensity-driven update in FP64 (Sec. 3.3); new array."""
+    a = np.ascontiguousarray(cube, dtype=np.float64).copy()
+    nx, ny, nz = _shape3(a)
+    rc = _load().orc_intensity_filter(a.ctypes.data, nx, ny, nz,
+                                      float(C[0]), float(C[1]), float(C[2]),
+                                      float(K), float(rms), float(tau),
+                                      int(n_iter))
+    if rc != 0:
+        raise ValueError("oracle intensity_filter rejected its arguments")
+    return a
+
+
+def stats(cube) -> dict:
+    """FP64 sums of an FP32 cube: sum, sum of squares, negative half."""
+    a = np.ascontiguousarray(cube, dtype=np.float32).reshape(-1)
+    out = np.zeros(4, dtype=np.float64)
+    _load().orc_stats(a.ctypes.data, a.size, out.ctypes.data)
+    return {"sum": out[0], "sumsq": out[1], "negsumsq": out[2],
+            "nneg": int(out[3]), "n": int(a.size)}
+
+
+def noise_rms(cube) -> float:
+    """Noise level: rms of the negative voxels, sqrt(sum_{I<0} I^2 / #{I<0}).
+
+    The paper uses the noise level "rms" to set K (Sec. 3.3) and takes it as
+    constant over the cube (Sec. 4) without stating the estimator.  Emission
+    is positive and the noise symmetric, so the negative half measures the
+    noise alone.  Returns 0.0 for a cube with no negative voxel.
+    """
+    s = stats(cube)
+    return math.sqrt(s["negsumsq"] / s["nneg"]) if s["nneg"] else 0.0
+
+
+# --------------------------------------------------------------------------
+# 2-byte storage (precision line).  The per-cube scale s is a power of two, so
+# I/s and q*s are exact; the only rounding is the one into the 2-byte format,
+# round-to-nearest-even in every case.
+# --------------------------------------------------------------------------
+I16_FRAC_BITS = 10   # int16 fixed point: step = s / 2^10, range +-32 s
+I16_MAX = 32767
+
+
+def pow2_scale(sigma: float) -> float:
+    """Per-cube scale: the power of two nearest the noise level (log2 rounded
+    half up).  A non-positive or non-finite sigma gives 1."""
+    if not (sigma > 0.0) or not math.isfinite(sigma):
+        return 1.0
+    return 2.0 ** math.floor(math.log2(sigma) + 0.5)
+
+
+def _f32_to_bf16_bits(x32: np.ndarray) -> np.ndarray:
+    """Round float32 to bfloat16 (nearest, ties to even) by its definition:
+    keep the upper 16 bits, rounding on the lower 16; NaN stays NaN."""
+    b = x32.view(np.uint32).astype(np.uint64)
+    lsb = (b >> 16) & 1
+    r = ((b + 0x7FFF + lsb) >> 16).astype(np.uint16)
+    nan = np.isnan(x32)
+    r[nan] = ((b[nan] >> 16) | 0x40).astype(np.uint16)
+    return r
+
+
+def quantize(cube, storage: str, scale: float) -> np.ndarray:
+    """q = RN(I / scale) in ``storage`` ('f16', 'bf16' or 'i16').
+
+    f16/bf16 return the 2-byte pattern as uint16; i16 returns int16 counts of
+    step = scale / 2^10, clamped to +-32767.
+    """
+    x = np.ascontiguousarray(cube, dtype=np.float32)
+    inv = np.float32(1.0 / scale)
+    if storage == "f16":
+        with np.errstate(over="ignore"):   # out of range rounds to +-inf
+            return (x * inv).astype(np.float16).view(np.uint16)
+    if storage == "bf16":
+        return _f32_to_bf16_bits((x * inv).astype(np.float32))
+    if storage == "i16":
+        step_inv = np.float32(2.0 ** I16_FRAC_BITS / scale)
+        q = np.rint((x * step_inv).astype(np.float64))
+        return np.clip(q, -I16_MAX, I16_MAX).astype(np.int16)
+    raise ValueError("storage must be 'f16', 'bf16' or 'i16'")
+
+
+def dequantize(q: np.ndarray, storage: str, scale: float) -> np.ndarray:
+    """Inverse of quantize: float32 value = stored value * scale (exact)."""
+    if storage == "f16":
+        v = q.view(np.float16).astype(np.float32)
+        return v * np.float32(scale)
+    if storage == "bf16":
+        v = (q.astype(np.uint32) << 16).view(np.float32)
+        return v * np.float32(scale)
+    if storage == "i16":
+        return q.astype(np.float32) * np.float32(scale / 2.0 ** I16_FRAC_BITS)
+    raise ValueError("storage must be 'f16', 'bf16' or 'i16'")
