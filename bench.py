@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Throughput of the anisotropic-diffusion hot path on GB300.
+
+Workload (one "step"): the 512 x 512 x 256 float32 H I cube (four inclined
+rotating disks and one faint tail in unit Gaussian noise, seed 0), resident in
+HBM:
+  a1  noise rms of the input (FP64 reduction) -> K = 1.0 * sigma
+  a3-a6  50 per-face Perona-Malik iterations, rational conductance,
+         dt = 1/8, zero-flux faces, out of place (the input stays intact)
+  a8  FP64 sum of the result (conservation check)
+Metric: Gvoxel-iterations per second = voxels * iterations / time.
+
+Multi-GPU (torchrun): every rank filters its own cube (independent problems,
+no collective on the data path; weak scaling); timing is the max over ranks.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("Gvoxel-iter/s and % of HBM roofline (FP32 vs FP16-stored) at stated error; "
+          "p50/p99 latency")
+UNIT = "Gvoxel-iter/s"
+N_ITER, DT, K_SIGMA, COND = 50, 1.0 / 8, 1.0, "rational"
+SHAPE = (256, 512, 512)
+WORKLOAD = ("cube512: 512x512x256 float32 (x, y, velocity), noise sigma=1, 4 disks "
+            "(i = 20/45/70/85 deg) + 1 faint tail, seed 0; rational g, K = 1.0 sigma "
+            "(GPU FP64 noise rms), dt = 1/8, 50 iterations, zero-flux faces")
+FALLBACK_HBM_GBS = 6800.0
+PROFILE = os.path.join(ROOT, "profiles", "pm_step_stream_cube512.md")
+KERNEL_SOURCES = ["paper_1609_03782_gb300/csrc/pm_stream.cu",
+                  "paper_1609_03782_gb300/csrc/afd_math.cuh",
+                  "paper_1609_03782_gb300/csrc/afd_ptx.cuh"]
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__,
+                                 formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["afd", "reference"], default="afd")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
+    t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid: str | None):
+        self.rows, self.proc, self.thread = [], None, None
+        self.uuid = device_uuid
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        rows = [r for r in self.rows if len(r) == 8]
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------
+def oracle_rate(cube, K, shape, repeats=1):
+    """Time the FP64 oracle (single thread) on the corner sub-cube `shape`."""
+    import oracle
+    nz, ny, nx = shape
+    sub = cube[:nz, :ny, :nx].copy()
+    oracle.build()
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        oracle.pm_filter(sub, K, DT, N_ITER, COND)
+    dt = time.perf_counter() - t0
+    return sub.size * N_ITER * repeats / dt / 1e9, dt
+
+
+def run_reference(args):
+    """The oracle as it stands, on host cores, on a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    cube = synth.cube512()
+    K = K_SIGMA * oracle.noise_rms(cube)
+    shape = (16, 64, 64)   # one step: 65,536 voxels x 50 iterations
+    for _ in range(args.warmup):
+        oracle_rate(cube, K, shape)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_rate(cube, K, shape)
+    el = time.perf_counter() - t0
+    n_vox = shape[0] * shape[1] * shape[2]
+    value = n_vox * N_ITER * args.steps / el / 1e9
+    sample = ("corner sub-cube %dx%dx%d of the 512x512x256 cube, 50 rational iterations "
+              "per step, FP64 single-threaded C oracle" % (shape[2], shape[1], shape[0]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+def run_afd(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_1609_03782_gb300 import afd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    cube = synth.cube512()
+    n_vox = cube.size
+    d_in = torch.from_numpy(cube).to(dev)
+    d_out = torch.empty_like(d_in)
+    out4 = torch.zeros(4, dtype=torch.float64, device=dev)
+    ctx = afd.afd_create(local)
+    stream = torch.cuda.current_stream(dev)
+
+    filt_events = []
+
+    def step(record):
+        sig = afd.afd_noise_rms(ctx, d_in)                        # a1
+        if record:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        afd.afd_filter_out(ctx, d_in, d_out, K_SIGMA * sig, DT, N_ITER, COND)  # a3-a6
+        if record:
+            e1.record(stream)
+            filt_events.append((e0, e1))
+        afd.afd_stats(ctx, d_out, out4)                           # a8
+        return sig
+
+    for _ in range(max(args.warmup, 0)):
+        sig = step(False)
+    torch.cuda.synchronize(dev)
+    afd.afd_sync(ctx)
+
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = afd.afd_launch_count(ctx)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        sig = step(True)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    afd.afd_sync(ctx)
+    launches = afd.afd_launch_count(ctx) - launches0
+    ms = max_over_ranks(t0.elapsed_time(t1))
+    filt_ms = sum(a.elapsed_time(b) for a, b in filt_events)
+    launch_ms = max_over_ranks(filt_ms / (args.steps * N_ITER))
+
+    # conservation of the last step's result (FP64 sums of the FP32 fields)
+    s_in = afd.afd_sum(ctx, d_in)
+    s_out = float(out4[0].item())
+    drift = abs(s_out - s_in) / float(np.abs(cube.astype(np.float64)).sum())
+
+    value = world * n_vox * N_ITER * args.steps / (ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    bytes_per_launch = 8.0 * n_vox       # read + write of one float32 cube
+    achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9
+
+    # ---- end to end through the host entry point: H2D + filter + D2H ----
+    K_host = K_SIGMA * sig
+    h_in = torch.from_numpy(cube).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    for _ in range(2):
+        afd.afd_filter_host(ctx, h_in, h_out, K_host, DT, N_ITER, COND)
+    barrier()
+    te = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        afd.afd_filter_host(ctx, h_in, h_out, K_host, DT, N_ITER, COND)
+    te = max_over_ranks(time.perf_counter() - te)
+    e2e_value = world * n_vox * N_ITER * args.e2e_steps / te / 1e9
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            shape = (128, 256, 256)
+            rate, secs = oracle_rate(cube, K_SIGMA * sig, shape)
+            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "FP64 C oracle, single thread, on the 256x256x128 corner "
+                             "sub-cube of the same cube, 50 rational iterations (%.1f s)"
+                             % secs}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD,
+                       "parallelism": "one independent cube per GPU" if world > 1 else "1 GPU",
+                       "l2": "inputs larger than L2 (268 MB cube in + 268 MB out + 268 MB "
+                             "ping-pong scratch vs 129 MB L2); no flush",
+                       "step": "a1 noise rms -> K, 50 filter iterations out of place, a8 FP64 "
+                               "sum of the result"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "kernel": "pm_step_stream (one iteration per launch)",
+                         "bytes_per_launch": bytes_per_launch,
+                         "launch_ms": launch_ms, "traffic": profiled_traffic()},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n_vox,
+                    "d2h_bytes_per_step": 4 * n_vox,
+                    "path": "afd_filter_host: pinned host in -> device -> 50 iterations -> "
+                            "pinned host out, synchronous"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "noise_rms": sig,
+            "sum_drift_rel": drift,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_afd(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

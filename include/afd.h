@@ -1,0 +1,199 @@
+/*
+ * afd.h — C ABI of the GB300 (sm_103a) anisotropic-diffusion library.
+ *
+ * The library filters 3-D H I spectral-line cubes with the gradient
+ * anisotropic-diffusion (Perona-Malik) filter of Punzo, van der Hulst &
+ * Roerdink, arXiv:1609.03782, Sec. 3.3 (eq. "perona", the gradient
+ * conductance printed after it, and the explicit n-step iteration that
+ * follows).  All arithmetic runs in hand-written CUDA kernels; the signatures
+ * below carry only plain pointers and sizes.
+ *
+ * Cube layout (every entry point): x fastest, element (x, y, z) at index
+ * x + nx*(y + ny*z), z the velocity axis.  "Device pointer" means memory the
+ * current CUDA context can address from the GPU (cudaMalloc, a torch CUDA
+ * tensor); "host pointer" means ordinary or pinned host memory.
+ *
+ * One filter iteration, per voxel p and each of its six face neighbours q
+ * along axis a with spacing h_a:
+ *     d  = (I[q] - I[p]) / h_a
+ *     I'[p] = I[p] + dt * sum_q g(d; K) * d / h_a
+ * with g(d; K) = exp(-(d/K)^2) (AFD_COND_EXPONENTIAL) or 1/(1+(d/K)^2)
+ * (AFD_COND_RATIONAL, the form printed in Sec. 3.3).  A face on the cube
+ * boundary carries no flux; the update is synchronous (every voxel of step
+ * i+1 reads step i only, the two-buffer memory model of Sec. 6); exactly
+ * n_iter steps are taken.  K = 0 is the identity; K = +inf is the discrete
+ * heat equation.
+ *
+ * Conventions shared by every entry point
+ *   - Ordering: work is enqueued on the context's stream and runs
+ *     asynchronously unless the entry point says it synchronises.  Argument
+ *     errors are reported synchronously and enqueue nothing.
+ *   - Errors: AFD_EINVAL for bad arguments (null pointers, sizes < 1, sizes
+ *     whose byte count overflows int64, non-finite or non-positive spacing or
+ *     dt, negative or NaN K, negative n_iter); AFD_ENOMEM when the library
+ *     cannot allocate its scratch; AFD_ECUDA when a CUDA call fails (the
+ *     CUDA error string is kept, see afd_last_error_string); AFD_ETIMEOUT
+ *     when a kernel's bounded wait expired (reported by afd_sync).
+ *   - Ownership: the caller owns every cube and output buffer it passes; the
+ *     context owns its scratch memory and frees it in afd_destroy.
+ *   - Threading: a context is not thread-safe; use one context per host
+ *     thread.
+ */
+#ifndef AFD_H
+#define AFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct afd_ctx afd_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    AFD_OK = 0,
+    AFD_EINVAL = 1,
+    AFD_ENOMEM = 2,
+    AFD_ECUDA = 3,
+    AFD_ETIMEOUT = 4,
+    AFD_EBUSY = 5
+} afd_status;
+
+/* Edge-stopping conductance g(d; K) (Sec. 3.3). */
+typedef enum {
+    AFD_COND_EXPONENTIAL = 0, /* exp(-(d/K)^2)                              */
+    AFD_COND_RATIONAL = 1     /* 1/(1+(d/K)^2), the paper's printed form    */
+} afd_conductance;
+
+/* Storage format of a cube (precision line).  The 2-byte formats hold
+ * value/scale with a power-of-two per-cube scale, rounded to nearest even. */
+typedef enum {
+    AFD_F32 = 0,    /* float32                                              */
+    AFD_F16 = 1,    /* IEEE binary16 of value/scale                        */
+    AFD_BF16 = 2,   /* bfloat16 of value/scale                             */
+    AFD_I16FIX = 3  /* int16 count of scale/1024 steps, clamped to +-32767 */
+} afd_storage;
+
+/* Kernel selection (tests and tuning; AUTO is the production choice). */
+typedef enum {
+    AFD_KERNEL_AUTO = 0,   /* streaming kernel when the layout allows it   */
+    AFD_KERNEL_SIMPLE = 1, /* one voxel per thread, any layout             */
+    AFD_KERNEL_STREAM = 2  /* TMA-staged x-y tiles streamed along z;
+                              needs nx % 4 == 0 and a 16-byte aligned cube */
+} afd_kernel;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * the context enqueues on (NULL: the legacy default stream of the device).
+ * *out receives the context.  Allocates a few bytes of device memory (the
+ * context's error word).  AFD_EINVAL if out is NULL or the device does not
+ * exist; AFD_ECUDA if the device cannot be initialised. */
+afd_status afd_create(afd_ctx **out, int device, void *cuda_stream);
+
+/* Free the context's scratch and the context itself after waiting for its
+ * stream.  NULL is accepted and returns AFD_OK. */
+afd_status afd_destroy(afd_ctx *ctx);
+
+/* Change the stream later calls enqueue on. */
+afd_status afd_set_stream(afd_ctx *ctx, void *cuda_stream);
+
+/* Choose the kernel family used by afd_filter (default AFD_KERNEL_AUTO).
+ * AFD_KERNEL_STREAM on a cube it cannot handle makes afd_filter return
+ * AFD_EINVAL.  All kernels give bit-identical results. */
+afd_status afd_set_kernel(afd_ctx *ctx, afd_kernel kernel);
+
+/* Tuning knob of the streaming kernel: the number of z planes one CTA
+ * streams per tile (0 = choose automatically from the cube shape and the
+ * device's SM count).  Results do not depend on it.  AFD_EINVAL if zc < 0. */
+afd_status afd_set_stream_zchunk(afd_ctx *ctx, int zc);
+
+/* Filter a float32 cube in place (Sec. 3.3: n_iter explicit iterations of
+ * the per-face scheme above).
+ *   cube     DEVICE pointer, nx*ny*nz floats, caller-owned, overwritten with
+ *            the result.
+ *   spacing  HOST pointer to (hx, hy, hz) > 0, or NULL for unit spacing.
+ *   K        conductance scale in the cube's intensity units (K = k*sigma for
+ *            a noise level sigma); 0 gives the identity, +inf the heat
+ *            equation.
+ *   dt       step (the paper's tau) > 0.  Steps beyond the stability bound
+ *            dt * sum_a 2/h_a^2 <= 1 are allowed (the paper's range reaches
+ *            tau = 0.0625 for its own weights) but lose the maximum
+ *            principle.
+ *   n_iter   number of iterations >= 0; 0 is a no-op.
+ * Uses 4*nx*ny*nz bytes of context scratch (allocated on first need, grown
+ * when needed, kept until afd_destroy) for the second buffer of the
+ * ping-pong; an odd n_iter ends with one device-to-device copy.
+ * Asynchronous. */
+afd_status afd_filter(afd_ctx *ctx, float *cube, int64_t nx, int64_t ny,
+                      int64_t nz, const float *spacing, float K, float dt,
+                      int n_iter, afd_conductance cond);
+
+/* Out-of-place afd_filter: reads `in`, writes the result to `out` (both
+ * DEVICE pointers to nx*ny*nz floats, caller-owned; `in` is not modified
+ * unless in == out, which is the in-place afd_filter).  Iterations alternate
+ * between `out` and context scratch so that the last one lands in `out`:
+ * no extra copy for any n_iter.  n_iter = 0 or K = 0 copies in to out.
+ * Asynchronous. */
+afd_status afd_filter_out(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
+                          int64_t nz, const float *spacing, float K, float dt, int n_iter,
+                          afd_conductance cond);
+
+/* afd_filter with the cube in pageable or pinned HOST memory: copies host_in
+ * to context-owned device memory, filters, and copies the result to
+ * host_out (host_in == host_out is allowed).  Synchronous: returns after the
+ * result is in host memory, so the timing of this call includes the
+ * host<->device transfers, as the paper's GPU timings do (Sec. 6).  Uses
+ * 8*nx*ny*nz bytes of context device memory besides the filter's scratch. */
+afd_status afd_filter_host(afd_ctx *ctx, const float *host_in, float *host_out, int64_t nx,
+                           int64_t ny, int64_t nz, const float *spacing, float K, float dt,
+                           int n_iter, afd_conductance cond);
+
+/* FP64 statistics of a float32 cube (noise level and conservation check).
+ *   cube     DEVICE pointer to n floats.
+ *   out4     DEVICE pointer to 4 doubles receiving, in this order:
+ *            sum I, sum I^2, sum over I<0 of I^2, number of I<0.
+ * Partial sums of 16 consecutive values are formed in float32 and every
+ * partial is accumulated in double in a fixed order, so repeated calls give
+ * bit-identical results.  Uses a few KB of context scratch.  Asynchronous. */
+afd_status afd_stats(afd_ctx *ctx, const float *cube, int64_t n,
+                     double *out4);
+
+/* Noise level of a float32 cube, sqrt(sum_{I<0} I^2 / #{I<0}) in FP64: the
+ * rms of the negative voxels (emission is positive, noise symmetric).  The
+ * paper sets K in units of this noise level "rms" (Sec. 3.3).  0 when no
+ * voxel is negative.  cube: DEVICE pointer; out: HOST pointer.
+ * Synchronises the context's stream. */
+afd_status afd_noise_rms(afd_ctx *ctx, const float *cube, int64_t n,
+                         double *out);
+
+/* FP64 sum of a float32 cube (conservation check: the per-face scheme moves
+ * intensity between voxels and never creates it).  cube: DEVICE pointer;
+ * out: HOST pointer.  Synchronises the context's stream. */
+afd_status afd_sum(afd_ctx *ctx, const float *cube, int64_t n, double *out);
+
+/* Wait for the context's stream and report the first asynchronous error:
+ * AFD_ECUDA for a CUDA error, AFD_ETIMEOUT when a kernel's bounded wait
+ * expired (the error word is then cleared). */
+afd_status afd_sync(afd_ctx *ctx);
+
+/* Diagnostic of the bounded-wait machinery: launches one kernel whose
+ * mbarrier wait can never complete and gives up after limit_ns nanoseconds
+ * (clamped to [1 us, 5 s]), recording the expiry in the context's error
+ * word.  The following afd_sync returns AFD_ETIMEOUT and the context stays
+ * usable.  The paper has no counterpart; it exists to test error reporting
+ * without hanging a GPU. */
+afd_status afd_selftest_wait(afd_ctx *ctx, int64_t limit_ns);
+
+/* Number of kernels this context has launched since it was created. */
+afd_status afd_launch_count(afd_ctx *ctx, uint64_t *out);
+
+/* Static description of a status code. */
+const char *afd_status_str(afd_status s);
+
+/* Text of the last CUDA error seen by this context ("" if none). */
+const char *afd_last_error_string(afd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFD_H */

@@ -1,0 +1,249 @@
+"""Python binding of libafd.so: argument marshalling only.
+
+Every function has the name of the C entry point it calls (include/afd.h) and
+does no arithmetic of its own: it turns tensors into pointers and sizes, the
+calling thread's current torch CUDA stream into the context's stream, and
+non-zero status codes into ``AfdError``.  Cubes are torch tensors shaped
+(nz, ny, nx), x fastest, as the C ABI lays them out.  There is no CPU
+fallback: if libafd.so is missing the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libafd.so")
+
+AFD_OK, AFD_EINVAL, AFD_ENOMEM, AFD_ECUDA, AFD_ETIMEOUT, AFD_EBUSY = range(6)
+COND = {"exponential": 0, "rational": 1}
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2, "i16": 3}
+KERNEL = {"auto": 0, "simple": 1, "stream": 2}
+
+
+class AfdError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        msg = "%s failed: %s" % (what, _lib.afd_status_str(status).decode())
+        if detail:
+            msg += " (%s)" % detail
+        super().__init__(msg)
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libafd.so is not built (run __graft_entry__.build() or "
+                          "python -m paper_1609_03782_gb300._build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, f32, c_int, dp = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_float,
+                               ctypes.c_int, ctypes.c_void_p)
+    sig = {
+        "afd_create": ([ctypes.POINTER(vp), c_int, vp], c_int),
+        "afd_destroy": ([vp], c_int),
+        "afd_set_stream": ([vp, vp], c_int),
+        "afd_set_kernel": ([vp, c_int], c_int),
+        "afd_set_stream_zchunk": ([vp, c_int], c_int),
+        "afd_filter": ([vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
+        "afd_filter_out": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
+        "afd_filter_host": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
+        "afd_selftest_wait": ([vp, i64], c_int),
+        "afd_stats": ([vp, vp, i64, vp], c_int),
+        "afd_noise_rms": ([vp, vp, i64, dp], c_int),
+        "afd_sum": ([vp, vp, i64, dp], c_int),
+        "afd_sync": ([vp], c_int),
+        "afd_launch_count": ([vp, ctypes.POINTER(ctypes.c_uint64)], c_int),
+        "afd_status_str": ([c_int], ctypes.c_char_p),
+        "afd_last_error_string": ([vp], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def exported_symbols():
+    """Names of the entry points this binding declares."""
+    return sorted(n for n in dir(_lib) if n.startswith("afd_"))
+
+
+class Context:
+    """Owns one afd_ctx*.  Not thread-safe: use one per host thread."""
+
+    def __init__(self, device: int = 0):
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        _check(_lib.afd_create(ctypes.byref(h), self.device, None), "afd_create", None)
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            _lib.afd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _check(status: int, what: str, ctx: Context | None):
+    if status != AFD_OK:
+        detail = ""
+        if ctx is not None and ctx.handle:
+            detail = _lib.afd_last_error_string(ctx.handle).decode()
+        raise AfdError(status, what, detail)
+
+
+def _use_current_stream(ctx: Context, t: torch.Tensor | None = None):
+    dev = t.device if t is not None and t.is_cuda else torch.device("cuda", ctx.device)
+    s = torch.cuda.current_stream(dev).cuda_stream
+    _check(_lib.afd_set_stream(ctx.handle, ctypes.c_void_p(s)), "afd_set_stream", ctx)
+
+
+def _cube_args(cube: torch.Tensor):
+    if cube.dim() != 3:
+        raise ValueError("cube must be 3-D, shaped (nz, ny, nx)")
+    if not cube.is_contiguous():
+        raise ValueError("cube must be contiguous")
+    nz, ny, nx = cube.shape
+    return ctypes.c_void_p(cube.data_ptr()), nx, ny, nz
+
+
+def _spacing(spacing):
+    if spacing is None:
+        return None
+    arr = (ctypes.c_float * 3)(*[float(s) for s in spacing])
+    return arr
+
+
+def afd_create(device: int = 0) -> Context:
+    return Context(device)
+
+
+def afd_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def afd_set_kernel(ctx: Context, kernel: str) -> None:
+    _check(_lib.afd_set_kernel(ctx.handle, KERNEL[kernel]), "afd_set_kernel", ctx)
+
+
+def afd_set_stream_zchunk(ctx: Context, zc: int) -> None:
+    _check(_lib.afd_set_stream_zchunk(ctx.handle, int(zc)), "afd_set_stream_zchunk", ctx)
+
+
+def afd_filter(ctx: Context, cube: torch.Tensor, K: float, dt: float, n_iter: int,
+               conductance: str = "rational", spacing=None) -> torch.Tensor:
+    """Filter a float32 CUDA tensor in place on the current stream; returns it."""
+    if cube.dtype != torch.float32 or not cube.is_cuda:
+        raise ValueError("afd_filter takes a float32 CUDA tensor")
+    p, nx, ny, nz = _cube_args(cube)
+    _use_current_stream(ctx, cube)
+    sp = _spacing(spacing)
+    _check(_lib.afd_filter(ctx.handle, p, nx, ny, nz, sp, float(K), float(dt), int(n_iter),
+                           COND[conductance]), "afd_filter", ctx)
+    return cube
+
+
+def afd_filter_out(ctx: Context, cube_in: torch.Tensor, cube_out: torch.Tensor, K: float,
+                   dt: float, n_iter: int, conductance: str = "rational",
+                   spacing=None) -> torch.Tensor:
+    """Out-of-place filter of float32 CUDA tensors on the current stream."""
+    for t in (cube_in, cube_out):
+        if t.dtype != torch.float32 or not t.is_cuda:
+            raise ValueError("afd_filter_out takes float32 CUDA tensors")
+    if cube_in.shape != cube_out.shape:
+        raise ValueError("input and output shapes differ")
+    p_in, nx, ny, nz = _cube_args(cube_in)
+    p_out, _, _, _ = _cube_args(cube_out)
+    _use_current_stream(ctx, cube_in)
+    _check(_lib.afd_filter_out(ctx.handle, p_in, p_out, nx, ny, nz, _spacing(spacing),
+                               float(K), float(dt), int(n_iter), COND[conductance]),
+           "afd_filter_out", ctx)
+    return cube_out
+
+
+def afd_filter_host(ctx: Context, host_in: torch.Tensor, host_out: torch.Tensor, K: float,
+                    dt: float, n_iter: int, conductance: str = "rational",
+                    spacing=None) -> torch.Tensor:
+    """Filter float32 CPU tensors (pinned or pageable) through the device;
+    synchronous, host<->device copies included."""
+    for t in (host_in, host_out):
+        if t.dtype != torch.float32 or t.is_cuda:
+            raise ValueError("afd_filter_host takes float32 CPU tensors")
+    if host_in.shape != host_out.shape:
+        raise ValueError("input and output shapes differ")
+    p_in, nx, ny, nz = _cube_args(host_in)
+    p_out, _, _, _ = _cube_args(host_out)
+    _use_current_stream(ctx)
+    _check(_lib.afd_filter_host(ctx.handle, p_in, p_out, nx, ny, nz, _spacing(spacing),
+                                float(K), float(dt), int(n_iter), COND[conductance]),
+           "afd_filter_host", ctx)
+    return host_out
+
+
+def afd_selftest_wait(ctx: Context, limit_ns: int) -> None:
+    """Launch the bounded-wait diagnostic; the next afd_sync must raise
+    AfdError with status AFD_ETIMEOUT."""
+    _use_current_stream(ctx)
+    _check(_lib.afd_selftest_wait(ctx.handle, int(limit_ns)), "afd_selftest_wait", ctx)
+
+
+def afd_stats(ctx: Context, cube: torch.Tensor, out4: torch.Tensor) -> torch.Tensor:
+    """Asynchronous FP64 stats into a 4-element float64 CUDA tensor:
+    sum, sum of squares, negative-half sum of squares, negative count."""
+    if out4.dtype != torch.float64 or not out4.is_cuda or out4.numel() < 4:
+        raise ValueError("out4 must be a float64 CUDA tensor of 4 elements")
+    if cube.dtype != torch.float32 or not cube.is_cuda or not cube.is_contiguous():
+        raise ValueError("afd_stats takes a contiguous float32 CUDA tensor")
+    _use_current_stream(ctx, cube)
+    _check(_lib.afd_stats(ctx.handle, ctypes.c_void_p(cube.data_ptr()), cube.numel(),
+                          ctypes.c_void_p(out4.data_ptr())), "afd_stats", ctx)
+    return out4
+
+
+def afd_noise_rms(ctx: Context, cube: torch.Tensor) -> float:
+    if cube.dtype != torch.float32 or not cube.is_cuda or not cube.is_contiguous():
+        raise ValueError("afd_noise_rms takes a contiguous float32 CUDA tensor")
+    _use_current_stream(ctx, cube)
+    out = ctypes.c_double()
+    _check(_lib.afd_noise_rms(ctx.handle, ctypes.c_void_p(cube.data_ptr()), cube.numel(),
+                              ctypes.byref(out)), "afd_noise_rms", ctx)
+    return out.value
+
+
+def afd_sum(ctx: Context, cube: torch.Tensor) -> float:
+    if cube.dtype != torch.float32 or not cube.is_cuda or not cube.is_contiguous():
+        raise ValueError("afd_sum takes a contiguous float32 CUDA tensor")
+    _use_current_stream(ctx, cube)
+    out = ctypes.c_double()
+    _check(_lib.afd_sum(ctx.handle, ctypes.c_void_p(cube.data_ptr()), cube.numel(),
+                        ctypes.byref(out)), "afd_sum", ctx)
+    return out.value
+
+
+def afd_sync(ctx: Context) -> None:
+    _check(_lib.afd_sync(ctx.handle), "afd_sync", ctx)
+
+
+def afd_launch_count(ctx: Context) -> int:
+    out = ctypes.c_uint64()
+    _check(_lib.afd_launch_count(ctx.handle, ctypes.byref(out)), "afd_launch_count", ctx)
+    return out.value
+
+
+def afd_status_str(status: int) -> str:
+    return _lib.afd_status_str(int(status)).decode()

@@ -1,0 +1,584 @@
+// C ABI of the anisotropic-diffusion library (declared in include/afd.h).
+//
+// Host-side logic only: argument validation, per-call coefficients, scratch
+// management, kernel selection, TMA descriptor encoding and the ping-pong
+// iteration driver.  Every step of the filter runs in the CUDA kernels of
+// this directory.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+#include <mutex>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include "../../include/afd.h"
+#include "afd_internal.h"
+
+struct afd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    int stream_bps = 0;          // streaming kernel CTAs per SM (occupancy)
+    int zc_hint = 0;             // streaming kernel z-chunk override (0 = auto)
+    afd_kernel kernel = AFD_KERNEL_AUTO;
+    int *d_err = nullptr;        // device error word (bounded-wait expiries)
+    float *scratch = nullptr;    // ping-pong partner buffer
+    size_t scratch_bytes = 0;
+    float *stage = nullptr;      // device copy for afd_filter_host
+    size_t stage_bytes = 0;
+    double *d_part = nullptr;    // stats partials
+    int part_blocks = 0;
+    double *d_out4 = nullptr;    // stats result (device)
+    double *h_out4 = nullptr;    // stats result (pinned host)
+    uint64_t launches = 0;
+    char errstr[256] = {0};
+};
+
+namespace {
+
+// ---- fault injection: AFD_FAULT=alloc:N makes the N-th scratch allocation
+// of the process fail as if the device were out of memory (host side only).
+std::mutex g_fault_mu;
+long g_alloc_calls = 0;
+
+bool injected_alloc_failure()
+{
+    const char *f = std::getenv("AFD_FAULT");
+    if (!f || std::strncmp(f, "alloc:", 6) != 0)
+        return false;
+    const long n = std::strtol(f + 6, nullptr, 10);
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    return ++g_alloc_calls == n;
+}
+
+afd_status cuda_fail(afd_ctx *ctx, cudaError_t e)
+{
+    if (ctx)
+        std::snprintf(ctx->errstr, sizeof(ctx->errstr), "%s: %s", cudaGetErrorName(e),
+                      cudaGetErrorString(e));
+    return AFD_ECUDA;
+}
+
+afd_status device_alloc(afd_ctx *ctx, void **p, size_t bytes)
+{
+    if (injected_alloc_failure())
+        return AFD_ENOMEM;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return AFD_ENOMEM;
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    return AFD_OK;
+}
+
+// Grow a context-owned device buffer to at least `bytes`.
+afd_status ensure_buffer(afd_ctx *ctx, float **buf, size_t *cap, size_t bytes)
+{
+    if (*cap >= bytes)
+        return AFD_OK;
+    if (*buf) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e);
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    void *p = nullptr;
+    afd_status st = device_alloc(ctx, &p, bytes);
+    if (st != AFD_OK)
+        return st;
+    *buf = static_cast<float *>(p);
+    *cap = bytes;
+    return AFD_OK;
+}
+
+bool dims_ok(int64_t nx, int64_t ny, int64_t nz)
+{
+    if (nx < 1 || ny < 1 || nz < 1)
+        return false;
+    const int64_t imax = std::numeric_limits<int>::max();
+    if (nx > imax || ny > imax || nz > imax)
+        return false;
+    const int64_t lim = std::numeric_limits<int64_t>::max() / 8;
+    if (nx > lim / ny || nx * ny > lim / nz)
+        return false;
+    return true;
+}
+
+bool params_ok(const float *spacing, float K, float dt, int n_iter, afd_conductance cond)
+{
+    if (cond != AFD_COND_EXPONENTIAL && cond != AFD_COND_RATIONAL)
+        return false;
+    if (spacing)
+        for (int a = 0; a < 3; ++a)
+            if (!(spacing[a] > 0.0f) || !std::isfinite(spacing[a]))
+                return false;
+    if (std::isnan(K) || K < 0.0f)
+        return false;
+    if (!(dt > 0.0f) || !std::isfinite(dt))
+        return false;
+    return n_iter >= 0;
+}
+
+// Per-axis coefficients in double, rounded once to float.  kappa is clamped
+// to FLT_MAX so that a tiny K cannot turn 0 * kappa into NaN.
+afd::Coef make_coef(const float *spacing, float K, float dt, afd_conductance cond, int *kind)
+{
+    const double h[3] = {spacing ? spacing[0] : 1.0, spacing ? spacing[1] : 1.0,
+                         spacing ? spacing[2] : 1.0};
+    afd::Coef c;
+    float kap[3], w[3];
+    const bool lin = std::isinf(K);
+    *kind = lin ? afd::COND_LIN : (cond == AFD_COND_EXPONENTIAL ? afd::COND_EXP : afd::COND_RAT);
+    const double log2e = 1.4426950408889634074;  // log2(e): exp(-u) = 2^(-u log2 e)
+    for (int a = 0; a < 3; ++a) {
+        double kk = 0.0;
+        if (!lin) {
+            const double kh = static_cast<double>(K) * h[a];
+            kk = (cond == AFD_COND_EXPONENTIAL ? log2e : 1.0) / (kh * kh);
+            if (!(kk <= static_cast<double>(std::numeric_limits<float>::max())))
+                kk = std::numeric_limits<float>::max();
+        }
+        kap[a] = static_cast<float>(kk);
+        w[a] = static_cast<float>(static_cast<double>(dt) / (h[a] * h[a]));
+    }
+    c.kx = kap[0];
+    c.ky = kap[1];
+    c.kz = kap[2];
+    c.wx = w[0];
+    c.wy = w[1];
+    c.wz = w[2];
+    return c;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependency on libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+afd_status encode_plane_map(afd_ctx *ctx, CUtensorMap *map, const float *ptr, int nx, int ny,
+                            int nz)
+{
+    std::call_once(g_encode_once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    if (!g_encode) {
+        std::snprintf(ctx->errstr, sizeof(ctx->errstr), "cuTensorMapEncodeTiled unavailable");
+        return AFD_ECUDA;
+    }
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(nx), static_cast<cuuint64_t>(ny),
+                                static_cast<cuuint64_t>(nz)};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(nx) * 4,
+                                   static_cast<cuuint64_t>(nx) * static_cast<cuuint64_t>(ny) * 4};
+    const cuuint32_t box[3] = {afd::kStreamTX + 8, afd::kStreamTY + 2, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(ptr), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        std::snprintf(ctx->errstr, sizeof(ctx->errstr), "cuTensorMapEncodeTiled failed (%d)",
+                      static_cast<int>(r));
+        return AFD_ECUDA;
+    }
+    return AFD_OK;
+}
+
+bool stream_kernel_fits(const float *a, const float *b, int64_t nx)
+{
+    return (nx % 4) == 0 && (reinterpret_cast<uintptr_t>(a) & 15u) == 0 &&
+           (reinterpret_cast<uintptr_t>(b) & 15u) == 0;
+}
+
+afd_status set_device(afd_ctx *ctx)
+{
+    cudaError_t e = cudaSetDevice(ctx->device);
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+}
+
+// The iteration driver shared by afd_filter, afd_filter_out and
+// afd_filter_host.  Pass i reads src_i and writes dst_i, src_0 = in,
+// src_i = dst_{i-1}.  Out of place (in != out) the destinations alternate
+// between `out` and scratch so that the last pass lands in `out`; in place
+// they alternate starting with scratch, and an odd count ends with a copy.
+afd_status filter_device(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
+                         int64_t nz, const float *spacing, float K, float dt, int n_iter,
+                         afd_conductance cond)
+{
+    const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (n_iter == 0 || K == 0.0f) {  // identity
+        if (in != out)
+            e = cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+    }
+    afd_status st = ensure_buffer(ctx, &ctx->scratch, &ctx->scratch_bytes, bytes);
+    if (st != AFD_OK)
+        return st;
+    int kind = 0;
+    const afd::Coef k = make_coef(spacing, K, dt, cond, &kind);
+
+    const bool inplace = (in == out);
+    auto dst_of = [&](int i) -> float * {
+        if (inplace)
+            return (i & 1) ? out : ctx->scratch;
+        return ((n_iter - 1 - i) & 1) ? ctx->scratch : out;
+    };
+    auto src_of = [&](int i) -> const float * { return i == 0 ? in : dst_of(i - 1); };
+
+    const bool fits = stream_kernel_fits(in, out, nx) &&
+                      (reinterpret_cast<uintptr_t>(ctx->scratch) & 15u) == 0;
+    bool use_stream = false;
+    if (ctx->kernel == AFD_KERNEL_STREAM) {
+        if (!fits)
+            return AFD_EINVAL;
+        use_stream = true;
+    } else if (ctx->kernel == AFD_KERNEL_AUTO) {
+        use_stream = fits;
+    }
+
+    if (use_stream) {
+        if (ctx->stream_bps == 0) {
+            e = afd::pm_stream_prepare();
+            if (e == cudaSuccess)
+                e = afd::pm_stream_occupancy(&ctx->stream_bps);
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e);
+            if (ctx->stream_bps < 1)
+                ctx->stream_bps = 1;
+        }
+        // one TMA descriptor per distinct source buffer
+        const float *srcs[3] = {in, out, ctx->scratch};
+        CUtensorMap maps[3];
+        for (int b = 0; b < 3; ++b) {
+            st = encode_plane_map(ctx, &maps[b], srcs[b], static_cast<int>(nx),
+                                  static_cast<int>(ny), static_cast<int>(nz));
+            if (st != AFD_OK)
+                return st;
+        }
+        const afd::StreamPlan plan =
+            afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny), static_cast<int>(nz),
+                                ctx->sm_count, ctx->stream_bps, ctx->zc_hint);
+        for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
+            const float *src = src_of(i);
+            const int m = (src == in) ? 0 : (src == out ? 1 : 2);
+            e = afd::launch_pm_stream(kind, maps[m], dst_of(i), static_cast<int>(nx),
+                                      static_cast<int>(ny), static_cast<int>(nz), k, plan,
+                                      ctx->d_err, ctx->stream);
+            ctx->launches++;
+        }
+    } else {
+        for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
+            e = afd::launch_pm_simple(kind, src_of(i), dst_of(i), static_cast<int>(nx),
+                                      static_cast<int>(ny), static_cast<int>(nz), k, ctx->stream);
+            ctx->launches++;
+        }
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    if (dst_of(n_iter - 1) != out) {
+        e = cudaMemcpyAsync(out, dst_of(n_iter - 1), bytes, cudaMemcpyDeviceToDevice,
+                            ctx->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e);
+    }
+    return AFD_OK;
+}
+
+afd_status stats_device(afd_ctx *ctx, const float *cube, int64_t n, double *out4)
+{
+    cudaError_t e = afd::launch_stats(cube, n, ctx->d_part, ctx->part_blocks, out4, ctx->stream);
+    ctx->launches += 2;
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+}
+
+afd_status stats_host(afd_ctx *ctx, const float *cube, int64_t n)
+{
+    afd_status st = stats_device(ctx, cube, n, ctx->d_out4);
+    if (st != AFD_OK)
+        return st;
+    cudaError_t e = cudaMemcpyAsync(ctx->h_out4, ctx->d_out4, 4 * sizeof(double),
+                                    cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+}
+
+}  // namespace
+
+extern "C" {
+
+afd_status afd_create(afd_ctx **out, int device, void *cuda_stream)
+{
+    if (!out)
+        return AFD_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return AFD_EINVAL;
+    }
+    afd_ctx *ctx = new (std::nothrow) afd_ctx();
+    if (!ctx)
+        return AFD_ENOMEM;
+    ctx->device = device;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        afd_status st = cuda_fail(ctx, e);
+        delete ctx;
+        return st;
+    }
+    ctx->part_blocks = ctx->sm_count * 4;
+    const size_t small = sizeof(int) * 32 + sizeof(double) * 4 +
+                         sizeof(double) * 4 * static_cast<size_t>(ctx->part_blocks);
+    void *p = nullptr;
+    afd_status st = device_alloc(ctx, &p, small);
+    if (st != AFD_OK) {
+        delete ctx;
+        return st;
+    }
+    ctx->d_err = static_cast<int *>(p);
+    ctx->d_out4 = reinterpret_cast<double *>(static_cast<char *>(p) + sizeof(int) * 32);
+    ctx->d_part = ctx->d_out4 + 4;
+    e = cudaMemset(ctx->d_err, 0, sizeof(int) * 32);
+    if (e == cudaSuccess)
+        e = cudaMallocHost(reinterpret_cast<void **>(&ctx->h_out4), 4 * sizeof(double));
+    if (e != cudaSuccess) {
+        st = cuda_fail(ctx, e);
+        cudaFree(ctx->d_err);
+        delete ctx;
+        return st;
+    }
+    *out = ctx;
+    return AFD_OK;
+}
+
+afd_status afd_destroy(afd_ctx *ctx)
+{
+    if (!ctx)
+        return AFD_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->scratch)
+        cudaFree(ctx->scratch);
+    if (ctx->stage)
+        cudaFree(ctx->stage);
+    if (ctx->d_err)
+        cudaFree(ctx->d_err);
+    if (ctx->h_out4)
+        cudaFreeHost(ctx->h_out4);
+    delete ctx;
+    return AFD_OK;
+}
+
+afd_status afd_set_stream(afd_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx)
+        return AFD_EINVAL;
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    return AFD_OK;
+}
+
+afd_status afd_set_kernel(afd_ctx *ctx, afd_kernel kernel)
+{
+    if (!ctx || (kernel != AFD_KERNEL_AUTO && kernel != AFD_KERNEL_SIMPLE &&
+                 kernel != AFD_KERNEL_STREAM))
+        return AFD_EINVAL;
+    ctx->kernel = kernel;
+    return AFD_OK;
+}
+
+afd_status afd_set_stream_zchunk(afd_ctx *ctx, int zc)
+{
+    if (!ctx || zc < 0)
+        return AFD_EINVAL;
+    ctx->zc_hint = zc;
+    return AFD_OK;
+}
+
+afd_status afd_filter(afd_ctx *ctx, float *cube, int64_t nx, int64_t ny, int64_t nz,
+                      const float *spacing, float K, float dt, int n_iter, afd_conductance cond)
+{
+    if (!ctx || !cube || !dims_ok(nx, ny, nz) || !params_ok(spacing, K, dt, n_iter, cond))
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    return filter_device(ctx, cube, cube, nx, ny, nz, spacing, K, dt, n_iter, cond);
+}
+
+afd_status afd_filter_out(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
+                          int64_t nz, const float *spacing, float K, float dt, int n_iter,
+                          afd_conductance cond)
+{
+    if (!ctx || !in || !out || !dims_ok(nx, ny, nz) ||
+        !params_ok(spacing, K, dt, n_iter, cond))
+        return AFD_EINVAL;
+    if (in != out) {  // partial overlap would corrupt the input mid-filter
+        const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
+        const char *a = reinterpret_cast<const char *>(in);
+        const char *b = reinterpret_cast<const char *>(out);
+        if (a < b + bytes && b < a + bytes)
+            return AFD_EINVAL;
+    }
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    return filter_device(ctx, in, out, nx, ny, nz, spacing, K, dt, n_iter, cond);
+}
+
+afd_status afd_filter_host(afd_ctx *ctx, const float *host_in, float *host_out, int64_t nx,
+                           int64_t ny, int64_t nz, const float *spacing, float K, float dt,
+                           int n_iter, afd_conductance cond)
+{
+    if (!ctx || !host_in || !host_out || !dims_ok(nx, ny, nz) ||
+        !params_ok(spacing, K, dt, n_iter, cond))
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
+    st = ensure_buffer(ctx, &ctx->stage, &ctx->stage_bytes, 2 * bytes);
+    if (st != AFD_OK)
+        return st;
+    float *d_in = ctx->stage;
+    float *d_out = ctx->stage + nx * ny * nz;
+    cudaError_t e = cudaMemcpyAsync(d_in, host_in, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    st = filter_device(ctx, d_in, d_out, nx, ny, nz, spacing, K, dt, n_iter, cond);
+    if (st != AFD_OK)
+        return st;
+    e = cudaMemcpyAsync(host_out, d_out, bytes, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    return afd_sync(ctx);
+}
+
+afd_status afd_stats(afd_ctx *ctx, const float *cube, int64_t n, double *out4)
+{
+    if (!ctx || !cube || !out4 || n < 1)
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    return stats_device(ctx, cube, n, out4);
+}
+
+afd_status afd_noise_rms(afd_ctx *ctx, const float *cube, int64_t n, double *out)
+{
+    if (!ctx || !cube || !out || n < 1)
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st == AFD_OK)
+        st = stats_host(ctx, cube, n);
+    if (st != AFD_OK)
+        return st;
+    const double nneg = ctx->h_out4[3];
+    *out = nneg > 0.0 ? std::sqrt(ctx->h_out4[2] / nneg) : 0.0;
+    return AFD_OK;
+}
+
+afd_status afd_sum(afd_ctx *ctx, const float *cube, int64_t n, double *out)
+{
+    if (!ctx || !cube || !out || n < 1)
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st == AFD_OK)
+        st = stats_host(ctx, cube, n);
+    if (st != AFD_OK)
+        return st;
+    *out = ctx->h_out4[0];
+    return AFD_OK;
+}
+
+afd_status afd_sync(afd_ctx *ctx)
+{
+    if (!ctx)
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    int code = 0;
+    e = cudaMemcpy(&code, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    if (code != 0) {
+        std::snprintf(ctx->errstr, sizeof(ctx->errstr), "bounded wait expired in a kernel (code %d)",
+                      code);
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        return AFD_ETIMEOUT;
+    }
+    return AFD_OK;
+}
+
+afd_status afd_selftest_wait(afd_ctx *ctx, int64_t limit_ns)
+{
+    if (!ctx)
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    if (limit_ns < 1000)
+        limit_ns = 1000;
+    if (limit_ns > 5000000000ll)
+        limit_ns = 5000000000ll;
+    cudaError_t e =
+        afd::launch_selftest_wait(static_cast<uint64_t>(limit_ns), ctx->d_err, ctx->stream);
+    ctx->launches++;
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+}
+
+afd_status afd_launch_count(afd_ctx *ctx, uint64_t *out)
+{
+    if (!ctx || !out)
+        return AFD_EINVAL;
+    *out = ctx->launches;
+    return AFD_OK;
+}
+
+const char *afd_status_str(afd_status s)
+{
+    switch (s) {
+    case AFD_OK:
+        return "AFD_OK";
+    case AFD_EINVAL:
+        return "AFD_EINVAL: invalid argument";
+    case AFD_ENOMEM:
+        return "AFD_ENOMEM: out of device memory";
+    case AFD_ECUDA:
+        return "AFD_ECUDA: CUDA error";
+    case AFD_ETIMEOUT:
+        return "AFD_ETIMEOUT: a kernel's bounded wait expired";
+    case AFD_EBUSY:
+        return "AFD_EBUSY: resource busy";
+    }
+    return "unknown afd_status";
+}
+
+const char *afd_last_error_string(afd_ctx *ctx)
+{
+    return ctx ? ctx->errstr : "";
+}
+
+}  // extern "C"
