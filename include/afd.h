@@ -183,6 +183,44 @@ afd_status afd_sync(afd_ctx *ctx);
  * without hanging a GPU. */
 afd_status afd_selftest_wait(afd_ctx *ctx, int64_t limit_ns);
 
+/* Largest cube afd_filter_noalloc accepts: 8,388,608 voxels, i.e. 32 MiB of
+ * float32 scratch (for example 256 x 256 x 128). */
+#define AFD_NOALLOC_MAX_VOXELS 8388608
+
+/* afd_filter_out for callers that cannot allocate GPU memory.
+ *
+ * The paper has no counterpart; this entry point exists for callers that may
+ * not call cudaMalloc: a host application that has already pooled every
+ * device byte for itself, a real-time loop where an allocation (and the
+ * device synchronisation it can cause) is not allowed, or a plug-in that is
+ * given no allocator.  Such callers cannot create an afd_ctx, which owns
+ * device memory, so this call takes no context.  It allocates nothing: the
+ * ping-pong scratch and the error word are fixed-size arrays inside the
+ * library's device image (AFD_NOALLOC_MAX_VOXELS floats, 32 MiB, plus 256
+ * bytes), which a GPU holds from the first call on it until the process
+ * exits.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ *   in, out      DEVICE pointers to nx*ny*nz floats, caller-owned (in == out
+ *                filters in place; other overlaps are rejected).
+ *   spacing, K, dt, n_iter, cond   as for afd_filter.
+ *   cuda_stream  cudaStream_t to run on, on the current device (NULL: the
+ *                legacy default stream).
+ * Results are bit-identical to afd_filter_out's.
+ * Sizes: nx*ny*nz > AFD_NOALLOC_MAX_VOXELS returns AFD_EINVAL before any GPU
+ * work, as do the argument errors of afd_filter_out.
+ * Set-up: the first call on each device (with that device current) looks up
+ * the arrays' device addresses; make that first call before any stream
+ * capture.
+ * Sharing: every call on a device uses the same arrays, which keep the last
+ * call's contents (the call clears its error word itself).  Calls whose work
+ * overlaps on the GPU (from several host threads or streams at once) race
+ * on the scratch and corrupt each other's results: serialise them.
+ * Synchronous: returns after the result is in `out`; AFD_ETIMEOUT if a
+ * kernel's bounded wait expired, AFD_ECUDA on a CUDA error. */
+afd_status afd_filter_noalloc(const float *in, float *out, int64_t nx, int64_t ny, int64_t nz,
+                              const float *spacing, float K, float dt, int n_iter,
+                              afd_conductance cond, void *cuda_stream);
+
 /* Number of kernels this context has launched since it was created. */
 afd_status afd_launch_count(afd_ctx *ctx, uint64_t *out);
 

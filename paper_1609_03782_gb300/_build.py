@@ -17,7 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libafd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["afd_api.cu", "pm_simple.cu", "pm_stream.cu", "reduce.cu", "selftest.cu"]
+SOURCES = ["afd_api.cu", "pm_simple.cu", "pm_stream.cu", "reduce.cu", "selftest.cu",
+           "noalloc.cu"]
 HEADERS = ["afd_math.cuh", "afd_ptx.cuh", "afd_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -49,6 +49,7 @@ def _load():
         "afd_filter_out": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_host": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_selftest_wait": ([vp, i64], c_int),
+        "afd_filter_noalloc": ([vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int, vp], c_int),
         "afd_stats": ([vp, vp, i64, vp], c_int),
         "afd_noise_rms": ([vp, vp, i64, dp], c_int),
         "afd_sum": ([vp, vp, i64, dp], c_int),
@@ -193,6 +194,35 @@ def afd_filter_host(ctx: Context, host_in: torch.Tensor, host_out: torch.Tensor,
                                 float(K), float(dt), int(n_iter), COND[conductance]),
            "afd_filter_host", ctx)
     return host_out
+
+
+NOALLOC_MAX_VOXELS = 8388608
+
+
+def afd_filter_noalloc(cube_in: torch.Tensor, cube_out: torch.Tensor, K: float, dt: float,
+                       n_iter: int, conductance: str = "rational", spacing=None) -> torch.Tensor:
+    """Filter without any GPU allocation, for callers that may not allocate
+    (no context needed; the library's fixed 32 MiB device scratch is used).
+
+    Runs on the current torch stream of the tensors' device and returns when
+    the result is in ``cube_out``.  Cubes above NOALLOC_MAX_VOXELS voxels are
+    rejected with AFD_EINVAL.  Calls that overlap on the GPU share the scratch
+    and must not run concurrently.
+    """
+    for t in (cube_in, cube_out):
+        if t.dtype != torch.float32 or not t.is_cuda:
+            raise ValueError("afd_filter_noalloc takes float32 CUDA tensors")
+    if cube_in.shape != cube_out.shape:
+        raise ValueError("input and output shapes differ")
+    p_in, nx, ny, nz = _cube_args(cube_in)
+    p_out, _, _, _ = _cube_args(cube_out)
+    with torch.cuda.device(cube_in.device):
+        s = torch.cuda.current_stream(cube_in.device).cuda_stream
+        status = _lib.afd_filter_noalloc(p_in, p_out, nx, ny, nz, _spacing(spacing), float(K),
+                                         float(dt), int(n_iter), COND[conductance],
+                                         ctypes.c_void_p(s))
+    _check(status, "afd_filter_noalloc", None)
+    return cube_out
 
 
 def afd_selftest_wait(ctx: Context, limit_ns: int) -> None:
