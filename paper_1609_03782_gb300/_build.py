@@ -21,8 +21,11 @@ SOURCES = ["afd_api.cu", "pm_simple.cu", "pm_stream.cu", "reduce.cu", "selftest.
            "noalloc.cu"]
 HEADERS = ["afd_math.cuh", "afd_ptx.cuh", "afd_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]
+# -fmad=false: no multiply/add contraction of scalar code anywhere; every FMA
+# the kernels want is written explicitly (afd_math.cuh also guards the packed
+# f32x2 products, which this flag does not cover, by forming them as FMAs).
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
+         "-Xcompiler", "-O2", "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]
 
 
 def nvcc() -> str:

@@ -127,37 +127,6 @@ bool params_ok(const float *spacing, float K, float dt, int n_iter, afd_conducta
     return n_iter >= 0;
 }
 
-// Per-axis coefficients in double, rounded once to float.  kappa is clamped
-// to FLT_MAX so that a tiny K cannot turn 0 * kappa into NaN.
-afd::Coef make_coef(const float *spacing, float K, float dt, afd_conductance cond, int *kind)
-{
-    const double h[3] = {spacing ? spacing[0] : 1.0, spacing ? spacing[1] : 1.0,
-                         spacing ? spacing[2] : 1.0};
-    afd::Coef c;
-    float kap[3], w[3];
-    const bool lin = std::isinf(K);
-    *kind = lin ? afd::COND_LIN : (cond == AFD_COND_EXPONENTIAL ? afd::COND_EXP : afd::COND_RAT);
-    const double log2e = 1.4426950408889634074;  // log2(e): exp(-u) = 2^(-u log2 e)
-    for (int a = 0; a < 3; ++a) {
-        double kk = 0.0;
-        if (!lin) {
-            const double kh = static_cast<double>(K) * h[a];
-            kk = (cond == AFD_COND_EXPONENTIAL ? log2e : 1.0) / (kh * kh);
-            if (!(kk <= static_cast<double>(std::numeric_limits<float>::max())))
-                kk = std::numeric_limits<float>::max();
-        }
-        kap[a] = static_cast<float>(kk);
-        w[a] = static_cast<float>(static_cast<double>(dt) / (h[a] * h[a]));
-    }
-    c.kx = kap[0];
-    c.ky = kap[1];
-    c.kz = kap[2];
-    c.wx = w[0];
-    c.wy = w[1];
-    c.wz = w[2];
-    return c;
-}
-
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no
 // link-time dependency on libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -228,7 +197,7 @@ afd_status filter_device(afd_ctx *ctx, const float *in, float *out, int64_t nx, 
     if (st != AFD_OK)
         return st;
     int kind = 0;
-    const afd::Coef k = make_coef(spacing, K, dt, cond, &kind);
+    const afd::Coef k = afd::make_coef(spacing, K, dt, cond == AFD_COND_EXPONENTIAL, &kind);
 
     const bool inplace = (in == out);
     auto dst_of = [&](int i) -> float * {

@@ -14,8 +14,9 @@ cudaError_t launch_pm_simple(int cond, const float *in, float *out, int nx, int 
                              const Coef &k, cudaStream_t stream);
 
 // ---- TMA-staged x-y tiles streamed along z (nx % 4 == 0, 16-B aligned) ----
-constexpr int kStreamTX = 64;   // interior tile width  (16 threads x float4)
-constexpr int kStreamTY = 16;   // interior tile height (one row per 16 threads)
+constexpr int kStreamTX = 64;   // interior tile width  (16 threads x 4 voxels)
+constexpr int kStreamTY = 32;   // interior tile height (16 threads x 2 rows)
+constexpr int kStreamSlots = 8; // planes in the shared-memory ring
 constexpr int kStreamConsumerWarps = 8;
 constexpr int kStreamThreads = kStreamConsumerWarps * 32 + 32;  // + 1 producer warp
 

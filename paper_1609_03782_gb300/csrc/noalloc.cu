@@ -21,7 +21,6 @@
 // same per-face arithmetic, so the results are bit-identical.
 #include <cmath>
 #include <cstdint>
-#include <limits>
 #include <mutex>
 
 #include <cuda.h>
@@ -151,32 +150,9 @@ extern "C" afd_status afd_filter_noalloc(const float *in, float *out, int64_t nx
         return e == cudaSuccess ? AFD_OK : AFD_ECUDA;
     }
 
-    // ---- coefficients: the per-axis kappa and weight of afd_filter ----
-    const double h[3] = {spacing ? spacing[0] : 1.0, spacing ? spacing[1] : 1.0,
-                         spacing ? spacing[2] : 1.0};
-    const bool lin = std::isinf(K);
-    const int kind = lin ? afd::COND_LIN
-                         : (cond == AFD_COND_EXPONENTIAL ? afd::COND_EXP : afd::COND_RAT);
-    const double log2e = 1.4426950408889634074;
-    float kap[3], w[3];
-    for (int a = 0; a < 3; ++a) {
-        double kk = 0.0;
-        if (!lin) {
-            const double kh = static_cast<double>(K) * h[a];
-            kk = (cond == AFD_COND_EXPONENTIAL ? log2e : 1.0) / (kh * kh);
-            if (!(kk <= static_cast<double>(std::numeric_limits<float>::max())))
-                kk = std::numeric_limits<float>::max();
-        }
-        kap[a] = static_cast<float>(kk);
-        w[a] = static_cast<float>(static_cast<double>(dt) / (h[a] * h[a]));
-    }
-    afd::Coef k;
-    k.kx = kap[0];
-    k.ky = kap[1];
-    k.kz = kap[2];
-    k.wx = w[0];
-    k.wy = w[1];
-    k.wz = w[2];
+    // ---- coefficients: those of afd_filter ----
+    int kind = 0;
+    const afd::Coef k = afd::make_coef(spacing, K, dt, cond == AFD_COND_EXPONENTIAL, &kind);
 
     // the error word must start at zero; the scratch is fully overwritten
     e = cudaMemsetAsync(s.err, 0, sizeof(int), stream);

@@ -4,8 +4,8 @@
 // gradient conductance).  Every thread reads its voxel and six face neighbours
 // straight from global memory (the L1/L2 caches supply the reuse) and writes
 // one voxel.  It handles any nx and any alignment; the streaming kernel is the
-// fast path.  The arithmetic is the canonical one of afd_math.cuh, so the
-// result is bit-identical to every other kernel.
+// fast path.  The arithmetic is the canonical one of afd_math.cuh (scalar
+// form), so the result is bit-identical to every other kernel.
 #include "afd_internal.h"
 
 namespace afd {
@@ -30,13 +30,13 @@ __global__ void __launch_bounds__(256)
     const float yp = y + 1 < ny ? in[p + sy] : c;
     const float zm = z > 0 ? in[p - sz] : c;
     const float zp = z + 1 < nz ? in[p + sz] : c;
-    const float fxm = -face_flux<C>(__fsub_rn(c, xm), k.kx);
-    const float fxp = face_flux<C>(__fsub_rn(xp, c), k.kx);
-    const float fym = -face_flux<C>(__fsub_rn(c, ym), k.ky);
-    const float fyp = face_flux<C>(__fsub_rn(yp, c), k.ky);
-    const float fzm = -face_flux<C>(__fsub_rn(c, zm), k.kz);
-    const float fzp = face_flux<C>(__fsub_rn(zp, c), k.kz);
-    out[p] = pm_update(c, fxm, fxp, fym, fyp, fzm, fzp, k);
+    const float gxm = face_flux<C>(__fsub_rn(c, xm), k.ax, k.bx, k.nz);
+    const float gxp = face_flux<C>(__fsub_rn(xp, c), k.ax, k.bx, k.nz);
+    const float gym = face_flux<C>(__fsub_rn(c, ym), k.ay, k.by, k.nz);
+    const float gyp = face_flux<C>(__fsub_rn(yp, c), k.ay, k.by, k.nz);
+    const float gzm = face_flux<C>(__fsub_rn(c, zm), k.az, k.bz, k.nz);
+    const float gzp = face_flux<C>(__fsub_rn(zp, c), k.az, k.bz, k.nz);
+    out[p] = pm_update(c, gxm, gxp, gym, gyp, gzm, gzp);
 }
 
 cudaError_t launch_pm_simple(int cond, const float *in, float *out, int nx, int ny, int nz,

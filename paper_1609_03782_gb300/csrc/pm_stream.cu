@@ -3,23 +3,26 @@
 // per-face discretisation of eq. "perona" with the gradient conductance).
 //
 // Design (sm_103a):
-//   * Persistent CTAs walk a static list of tiles: a tile is 64 (x) x 16 (y)
+//   * Persistent CTAs walk a static list of tiles: a tile is 64 (x) x 32 (y)
 //     columns over a chunk of zc planes.  Tiles are numbered x fastest, then
-//     y, then z-chunk, so CTAs running at the same time share halo rows and
-//     planes through L2.
+//     y, then z-chunk, so CTAs running at the same time share halo rows
+//     through L2.
 //   * Warp 8 is the producer: one lane issues a 3-D TMA load
 //     (cp.async.bulk.tensor) per plane of the tile's chunk, plus one halo
 //     plane below and above, into a ring of shared-memory slots guarded by
-//     "full" / "empty" mbarriers.  A slot holds the plane's 64 x 16 interior
+//     "full" / "empty" mbarriers.  A slot holds the plane's 64 x 32 interior
 //     with a one-row halo in y and a four-float halo in x (the TMA x
 //     coordinate must be a multiple of 4 floats); elements outside the cube
 //     are zero-filled by the TMA unit and never used.
-//   * Warps 0-7 consume: thread (qx, ry) owns the 4 x-consecutive voxels
-//     x0+4qx..x0+4qx+3 of row y0+ry.  Its voxels of the planes below and
-//     above live in registers (the z neighbours roll through registers), the
-//     x and y neighbours come from the plane's slot.  Each x face inside the
-//     quad and each z face is evaluated once and used for both voxels that
-//     share it (5 x-, 8 y- and 4 z-face conductances per 4 voxels).
+//   * Warps 0-7 consume: thread (qx, ry) owns a 4 (x) x 2 (y) block of
+//     voxels, x0+4qx.., rows y0+2ry and y0+2ry+1.  The block's voxels of the
+//     plane below and above roll through registers; x and y neighbours come
+//     from the plane's slot.  Every face inside the block and every z face is
+//     evaluated once for both voxels (30 conductances per 8 voxels), and the
+//     arithmetic runs on packed f32x2 instructions (two voxels per
+//     instruction; each lane rounds exactly like the scalar canonical form,
+//     so results are bit-identical to the one-voxel-per-thread kernel).
+//   * Tiles that touch no cube face take a path without boundary selects.
 //   * Results go straight to global memory with 16-byte stores.
 // Requirements checked by the host: nx % 4 == 0, 16-byte aligned pointers.
 // Every mbarrier wait is bounded (afd_ptx.cuh).
@@ -31,14 +34,15 @@ namespace {
 
 constexpr int TX = kStreamTX;
 constexpr int TY = kStreamTY;
-constexpr int PX = TX + 8;                                // floats per slot row
-constexpr int PY = TY + 2;                                // rows per slot
-constexpr uint32_t BOX_BYTES = PX * PY * sizeof(float);   // one TMA box
+constexpr int PX = TX + 8;                                 // floats per slot row
+constexpr int PY = TY + 2;                                 // rows per slot
+constexpr uint32_t BOX_BYTES = PX * PY * sizeof(float);    // one TMA box
 constexpr int SLOT_BYTES = (BOX_BYTES + 127) / 128 * 128;  // 128-B aligned slots
 constexpr int SLOT_FLOATS = SLOT_BYTES / 4;
-constexpr int NSLOT = 6;
+constexpr uint32_t NSLOT = kStreamSlots;                   // power of two
 constexpr int NCW = kStreamConsumerWarps;
-static_assert(TX == 16 * 4 && TY * 16 == NCW * 32, "thread mapping");
+static_assert(TX == 16 * 4 && TY == 2 * 16 && NCW * 32 == 256, "thread mapping");
+static_assert((NSLOT & (NSLOT - 1)) == 0, "ring size must be a power of two");
 
 struct TileCoord {
     int x0, y0, z0, z1, zlo, np;
@@ -63,23 +67,61 @@ __device__ __forceinline__ TileCoord decode_tile(int64_t t, int tiles_x, int til
     return c;
 }
 
-template <int C>
-__device__ __forceinline__ float4 flux4(float4 lo, float4 hi, float kappa)
+// Four voxels of one row as two packed pairs: (x, x+1) and (x+2, x+3).
+struct Q {
+    f2_t a, b;
+};
+
+__device__ __forceinline__ Q lds_q(const float *p)
 {
-    return make_float4(face_flux<C>(__fsub_rn(hi.x, lo.x), kappa),
-                       face_flux<C>(__fsub_rn(hi.y, lo.y), kappa),
-                       face_flux<C>(__fsub_rn(hi.z, lo.z), kappa),
-                       face_flux<C>(__fsub_rn(hi.w, lo.w), kappa));
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return {f2_pack(v.x, v.y), f2_pack(v.z, v.w)};
+}
+
+__device__ __forceinline__ Q q_sub(Q u, Q v) { return {f2_sub(u.a, v.a), f2_sub(u.b, v.b)}; }
+
+template <int C>
+__device__ __forceinline__ Q q_flux(Q d, f2_t A2, f2_t B2, f2_t Z2)
+{
+    return {face_flux2<C>(d.a, A2, B2, Z2), face_flux2<C>(d.b, A2, B2, Z2)};
+}
+
+__device__ __forceinline__ void stg_q(float *p, Q v)
+{
+    float4 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(v.a));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.z), "=f"(o.w) : "l"(v.b));
+    *reinterpret_cast<float4 *>(p) = o;
+}
+
+struct Packed {
+    f2_t ax, ay, az, bx, by, bz, z;
+};
+
+// x fluxes of one row: voxel sums s_x = G_x+ - G_x- for the quad (c0..c3)
+// given its left neighbour xl and right neighbour xr.  The x faces are
+// F0 (xl|c0) F1 (c0|c1) F2 (c1|c2) F3 (c2|c3) F4 (c3|xr); F4 is passed in
+// (computed for both rows in one packed op).
+template <int C>
+__device__ __forceinline__ Q x_sums(Q c, float xl, float f4, const Packed &k)
+{
+    float c0, c1, c2, c3;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(c0), "=f"(c1) : "l"(c.a));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(c2), "=f"(c3) : "l"(c.b));
+    const f2_t f01 = face_flux2<C>(f2_sub(c.a, f2_pack(xl, c0)), k.ax, k.bx, k.z);  // (F0, F1)
+    const f2_t f23 = face_flux2<C>(f2_sub(c.b, f2_pack(c1, c2)), k.ax, k.bx, k.z);  // (F2, F3)
+    const f2_t f12 = f2_pack(f2_hi(f01), f2_lo(f23));
+    const f2_t f34 = f2_pack(f2_hi(f23), f4);
+    return {f2_sub(f12, f01), f2_sub(f34, f23)};
 }
 
 template <int C>
-__global__ void __launch_bounds__(kStreamThreads, 3)
+__global__ void __launch_bounds__(kStreamThreads, 2)
     pm_step_stream(const __grid_constant__ CUtensorMap tmap, float *__restrict__ out, int nx,
-                   int ny, int nz, int tiles_x, int tiles_y, int zc, int64_t ntiles, Coef k,
+                   int ny, int nz, int tiles_x, int tiles_y, int zc, int64_t ntiles, Coef kc,
                    int *err)
 {
     extern __shared__ unsigned char smem_raw[];
-    // 128-byte align the slot array (TMA destination)
     const uint32_t base = smem_u32(smem_raw);
     unsigned char *smem = smem_raw + ((128u - (base & 127u)) & 127u);
     float *slots = reinterpret_cast<float *>(smem);
@@ -89,7 +131,7 @@ __global__ void __launch_bounds__(kStreamThreads, 3)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NSLOT; ++i) {
+        for (uint32_t i = 0; i < NSLOT; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], NCW);
         }
@@ -104,7 +146,7 @@ __global__ void __launch_bounds__(kStreamThreads, 3)
             for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
                 const TileCoord tc = decode_tile(t, tiles_x, tiles_y, zc, nz);
                 for (int j = 0; j < tc.np; ++j, ++kk) {
-                    const uint32_t slot = kk % NSLOT;
+                    const uint32_t slot = kk & (NSLOT - 1);
                     const uint32_t use = kk / NSLOT;
                     if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1u, err, kErrWaitEmpty))
                         return;
@@ -118,86 +160,138 @@ __global__ void __launch_bounds__(kStreamThreads, 3)
     }
 
     // ---------------- consumers ----------------
+    Packed k;
+    k.ax = f2_pack(kc.ax, kc.ax);
+    k.ay = f2_pack(kc.ay, kc.ay);
+    k.az = f2_pack(kc.az, kc.az);
+    k.bx = f2_pack(kc.bx, kc.bx);
+    k.by = f2_pack(kc.by, kc.by);
+    k.bz = f2_pack(kc.bz, kc.bz);
+    k.z = f2_pack(kc.nz, kc.nz);
     const int qx = threadIdx.x & 15;
     const int ry = threadIdx.x >> 4;
+    const int r0 = 1 + 2 * ry;                      // slot row of the first row
+    const int cen0 = r0 * PX + 4 + 4 * qx;          // quad of row 0 in a slot
+    const int cen1 = cen0 + PX;                     // quad of row 1
     uint32_t kk = 0;
+
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const TileCoord tc = decode_tile(t, tiles_x, tiles_y, zc, nz);
         const int x = tc.x0 + 4 * qx;
-        const int y = tc.y0 + ry;
-        const bool active = (x < nx) && (y < ny);
+        const int ya = tc.y0 + 2 * ry;  // row 0
+        const int yb = ya + 1;          // row 1
+        const bool act0 = (x < nx) && (ya < ny);
+        const bool act1 = (x < nx) && (yb < ny);
+        const bool edge = (tc.x0 == 0) || (tc.x0 + TX >= nx) || (tc.y0 == 0) ||
+                          (tc.y0 + TY >= ny);
         const uint32_t kbase = kk;
-        const int cen = (ry + 1) * PX + 4 + 4 * qx;  // this thread's quad in a slot
+        const int64_t row_stride = nx;
+        float *out0 = out + (static_cast<int64_t>(ya) * nx + x);
 
 #define RING(z) (kbase + static_cast<uint32_t>((z) - tc.zlo))
-#define SLOT_PTR(r) (slots + ((r) % NSLOT) * SLOT_FLOATS)
+#define SLOT_PTR(r) (slots + ((r) & (NSLOT - 1)) * SLOT_FLOATS)
 #define WAIT_FULL(r)                                                                     \
-    if (!mbar_wait(&full[(r) % NSLOT], ((r) / NSLOT) & 1u, err, kErrWaitFull))           \
+    if (!mbar_wait(&full[(r) & (NSLOT - 1)], ((r) / NSLOT) & 1u, err, kErrWaitFull))      \
         return;
 #define RELEASE(r)                                                                       \
     do {                                                                                 \
         __syncwarp();                                                                    \
         if (lane == 0)                                                                   \
-            mbar_arrive(&empty[(r) % NSLOT]);                                            \
+            mbar_arrive(&empty[(r) & (NSLOT - 1)]);                                      \
     } while (0)
 
-        float4 cur, fzprev;
+        Q cur0, cur1, fb0, fb1;  // current plane and the flux through its lower z face
         {
-            const uint32_t r0 = RING(tc.z0);
+            const uint32_t rz = RING(tc.z0);
             if (tc.z0 > 0) {
                 const uint32_t rb = RING(tc.z0 - 1);
                 WAIT_FULL(rb);
-                const float4 prev = *reinterpret_cast<const float4 *>(SLOT_PTR(rb) + cen);
-                WAIT_FULL(r0);
-                cur = *reinterpret_cast<const float4 *>(SLOT_PTR(r0) + cen);
-                fzprev = flux4<C>(prev, cur, k.kz);
+                const Q p0 = lds_q(SLOT_PTR(rb) + cen0);
+                const Q p1 = lds_q(SLOT_PTR(rb) + cen1);
+                WAIT_FULL(rz);
+                cur0 = lds_q(SLOT_PTR(rz) + cen0);
+                cur1 = lds_q(SLOT_PTR(rz) + cen1);
+                fb0 = q_flux<C>(q_sub(cur0, p0), k.az, k.bz, k.z);
+                fb1 = q_flux<C>(q_sub(cur1, p1), k.az, k.bz, k.z);
                 RELEASE(rb);
             } else {
-                WAIT_FULL(r0);
-                cur = *reinterpret_cast<const float4 *>(SLOT_PTR(r0) + cen);
-                fzprev = flux4<C>(cur, cur, k.kz);  // zero flux through z = 0
+                WAIT_FULL(rz);
+                cur0 = lds_q(SLOT_PTR(rz) + cen0);
+                cur1 = lds_q(SLOT_PTR(rz) + cen1);
+                fb0 = q_flux<C>(q_sub(cur0, cur0), k.az, k.bz, k.z);  // zero flux at z = 0
+                fb1 = q_flux<C>(q_sub(cur1, cur1), k.az, k.bz, k.z);
             }
         }
 
         for (int z = tc.z0; z < tc.z1; ++z) {
             const uint32_t rc = RING(z);
             const float *s = SLOT_PTR(rc);
-            float4 nxt, fznext;
+            // ---- z: the plane above and the flux through the upper face
+            Q n0, n1, fa0, fa1;
             if (z + 1 < nz) {
                 const uint32_t rn = RING(z + 1);
                 WAIT_FULL(rn);
-                nxt = *reinterpret_cast<const float4 *>(SLOT_PTR(rn) + cen);
-                fznext = flux4<C>(cur, nxt, k.kz);
+                n0 = lds_q(SLOT_PTR(rn) + cen0);
+                n1 = lds_q(SLOT_PTR(rn) + cen1);
             } else {
-                nxt = cur;
-                fznext = flux4<C>(cur, cur, k.kz);  // zero flux through z = nz-1
+                n0 = cur0;  // zero flux at z = nz-1
+                n1 = cur1;
             }
-            // x neighbours of the quad, y neighbour quads (own value at the faces)
-            const float xl = (x > 0) ? s[cen - 1] : cur.x;
-            const float xr = (x + 4 < nx) ? s[cen + 4] : cur.w;
-            const float4 dn = (y > 0) ? *reinterpret_cast<const float4 *>(s + cen - PX) : cur;
-            const float4 up = (y + 1 < ny) ? *reinterpret_cast<const float4 *>(s + cen + PX) : cur;
+            fa0 = q_flux<C>(q_sub(n0, cur0), k.az, k.bz, k.z);
+            fa1 = q_flux<C>(q_sub(n1, cur1), k.az, k.bz, k.z);
 
-            const float f0 = face_flux<C>(__fsub_rn(cur.x, xl), k.kx);
-            const float f1 = face_flux<C>(__fsub_rn(cur.y, cur.x), k.kx);
-            const float f2 = face_flux<C>(__fsub_rn(cur.z, cur.y), k.kx);
-            const float f3 = face_flux<C>(__fsub_rn(cur.w, cur.z), k.kx);
-            const float f4 = face_flux<C>(__fsub_rn(xr, cur.w), k.kx);
-            const float4 fyl = flux4<C>(dn, cur, k.ky);
-            const float4 fyu = flux4<C>(cur, up, k.ky);
+            // ---- neighbours in the plane (own value across a cube face)
+            Q dn = lds_q(s + cen0 - PX);
+            Q up = lds_q(s + cen1 + PX);
+            Q mid = cur1;
+            float xl0 = s[cen0 - 1], xr0 = s[cen0 + 4];
+            float xl1 = s[cen1 - 1], xr1 = s[cen1 + 4];
+            if (edge) {
+                float c0a = f2_lo(cur0.a), c3a = f2_hi(cur0.b);
+                float c0b = f2_lo(cur1.a), c3b = f2_hi(cur1.b);
+                if (ya == 0)
+                    dn = cur0;
+                if (yb >= ny)
+                    mid = cur0;
+                if (yb + 1 >= ny)
+                    up = cur1;
+                if (x == 0) {
+                    xl0 = c0a;
+                    xl1 = c0b;
+                }
+                if (x + 4 >= nx) {
+                    xr0 = c3a;
+                    xr1 = c3b;
+                }
+            }
 
-            float4 o;
-            o.x = pm_update(cur.x, -f0, f1, -fyl.x, fyu.x, -fzprev.x, fznext.x, k);
-            o.y = pm_update(cur.y, -f1, f2, -fyl.y, fyu.y, -fzprev.y, fznext.y, k);
-            o.z = pm_update(cur.z, -f2, f3, -fyl.z, fyu.z, -fzprev.z, fznext.z, k);
-            o.w = pm_update(cur.w, -f3, f4, -fyl.w, fyu.w, -fzprev.w, fznext.w, k);
-            if (active)
-                *reinterpret_cast<float4 *>(
-                    out + (static_cast<int64_t>(z) * ny + y) * static_cast<int64_t>(nx) + x) = o;
+            // ---- y: faces (dn|row0), (row0|row1), (row1|up)
+            const Q fdn = q_flux<C>(q_sub(cur0, dn), k.ay, k.by, k.z);
+            const Q fmid = q_flux<C>(q_sub(mid, cur0), k.ay, k.by, k.z);
+            const Q fup = q_flux<C>(q_sub(up, cur1), k.ay, k.by, k.z);
+
+            // ---- x: F4 of both rows in one packed op, then the in-row faces
+            const f2_t c3p = f2_pack(f2_hi(cur0.b), f2_hi(cur1.b));
+            const f2_t f4 = face_flux2<C>(f2_sub(f2_pack(xr0, xr1), c3p), k.ax, k.bx, k.z);
+            const Q sx0 = x_sums<C>(cur0, xl0, f2_lo(f4), k);
+            const Q sx1 = x_sums<C>(cur1, xl1, f2_hi(f4), k);
+
+            // ---- update: I' = I + ((s_x + s_y) + s_z)
+            const Q o0 = {pm_update2(cur0.a, sx0.a, f2_sub(fmid.a, fdn.a), f2_sub(fa0.a, fb0.a)),
+                          pm_update2(cur0.b, sx0.b, f2_sub(fmid.b, fdn.b), f2_sub(fa0.b, fb0.b))};
+            const Q o1 = {pm_update2(cur1.a, sx1.a, f2_sub(fup.a, fmid.a), f2_sub(fa1.a, fb1.a)),
+                          pm_update2(cur1.b, sx1.b, f2_sub(fup.b, fmid.b), f2_sub(fa1.b, fb1.b))};
+            float *po = out0 + static_cast<int64_t>(z) * ny * row_stride;
+            if (act0)
+                stg_q(po, o0);
+            if (act1)
+                stg_q(po + row_stride, o1);
 
             RELEASE(rc);
-            cur = nxt;
-            fzprev = fznext;
+            cur0 = n0;
+            cur1 = n1;
+            fb0 = fa0;
+            fb1 = fa1;
         }
         if (tc.z1 < nz)
             RELEASE(RING(tc.z1));  // the halo plane above the chunk
