@@ -46,9 +46,15 @@ def up_to_date() -> bool:
     return os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input()
 
 
+def _extra_flags():
+    """Extra nvcc flags from AFD_NVCC_FLAGS (tuning builds, e.g.
+    -DAFD_STREAM_SLOTS=4 -DAFD_STREAM_MIN_BLOCKS=3)."""
+    return os.environ.get("AFD_NVCC_FLAGS", "").split()
+
+
 def _compile(src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [nvcc(), *ARCH, *FLAGS, *_extra_flags(), "-c", os.path.join(CSRC, src), "-o", obj]
     if verbose:
         cmd[1:1] = ["-Xptxas", "-v"]
     res = subprocess.run(cmd, capture_output=True, text=True)

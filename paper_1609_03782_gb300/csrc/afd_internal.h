@@ -16,7 +16,14 @@ cudaError_t launch_pm_simple(int cond, const float *in, float *out, int nx, int 
 // ---- TMA-staged x-y tiles streamed along z (nx % 4 == 0, 16-B aligned) ----
 constexpr int kStreamTX = 64;   // interior tile width  (16 threads x 4 voxels)
 constexpr int kStreamTY = 32;   // interior tile height (16 threads x 2 rows)
-constexpr int kStreamSlots = 8; // planes in the shared-memory ring
+#ifndef AFD_STREAM_SLOTS
+#define AFD_STREAM_SLOTS 8
+#endif
+#ifndef AFD_STREAM_MIN_BLOCKS
+#define AFD_STREAM_MIN_BLOCKS 2
+#endif
+constexpr int kStreamSlots = AFD_STREAM_SLOTS;          // planes in the smem ring
+constexpr int kStreamMinBlocks = AFD_STREAM_MIN_BLOCKS; // CTAs per SM to fit
 constexpr int kStreamConsumerWarps = 8;
 constexpr int kStreamThreads = kStreamConsumerWarps * 32 + 32;  // + 1 producer warp
 

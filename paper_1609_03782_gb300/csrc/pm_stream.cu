@@ -116,7 +116,7 @@ __device__ __forceinline__ Q x_sums(Q c, float xl, float f4, const Packed &k)
 }
 
 template <int C>
-__global__ void __launch_bounds__(kStreamThreads, 2)
+__global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
     pm_step_stream(const __grid_constant__ CUtensorMap tmap, float *__restrict__ out, int nx,
                    int ny, int nz, int tiles_x, int tiles_y, int zc, int64_t ntiles, Coef kc,
                    int *err)
