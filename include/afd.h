@@ -147,6 +147,50 @@ afd_status afd_filter_host(afd_ctx *ctx, const float *host_in, float *host_out, 
                            int64_t ny, int64_t nz, const float *spacing, float K, float dt,
                            int n_iter, afd_conductance cond);
 
+/* Round a float32 cube into a 2-byte storage format (precision line): out[i]
+ * = RN(in[i] / scale) in float16 or bfloat16, or RN(in[i] * 1024 / scale)
+ * as int16 clamped to +-32767; nearest, ties to even.
+ *   in       DEVICE pointer to n floats.
+ *   out      DEVICE pointer to n 2-byte elements.
+ *   storage  AFD_F16, AFD_BF16 or AFD_I16FIX (AFD_F32 is rejected).
+ *   scale    the cube's power-of-two scale (> 0, finite; e.g. the power of
+ *            two nearest the noise level), so the division is exact.
+ * The paper argues float precision suffices for H I data (Sec. 6); the
+ * 2-byte formats halve the bytes again.  Asynchronous; AFD_EINVAL for a
+ * non-power-of-two scale or n < 1. */
+afd_status afd_quantize(afd_ctx *ctx, const float *in, void *out, int64_t n,
+                        afd_storage storage, float scale);
+
+/* Inverse of afd_quantize: out[i] = stored value * scale (exact).  in: DEVICE
+ * pointer to n 2-byte elements; out: DEVICE pointer to n floats.
+ * Asynchronous. */
+afd_status afd_dequantize(afd_ctx *ctx, const void *in, float *out, int64_t n,
+                          afd_storage storage, float scale);
+
+/* The filter on a cube in any storage format, with T = t_block iterations
+ * fused per pass over HBM (temporal blocking).
+ *   in, out   DEVICE pointers to nx*ny*nz elements of `storage` (in == out
+ *             filters in place; other overlaps are rejected).
+ *   storage   AFD_F32, AFD_F16, AFD_BF16 or AFD_I16FIX.
+ *   scale     the cube's power-of-two scale (ignored for AFD_F32).
+ *   K         in the cube's value units (value = stored value * scale).
+ *   spacing, dt, n_iter, cond   as for afd_filter.
+ *   t_block   1, 2, 4 or 8 (0 = 4 for 2-byte storage, 2 for float32).
+ * Each pass reads the stored cube, runs its iterations in float32 with the
+ * arithmetic of afd_filter, and rounds the result once into the storage
+ * format; n_iter = (n_iter / T) passes of depth T, the remainder as passes
+ * of depth 4, 2, 1 (at most T).  A pass is bit-identical to dequantise ->
+ * that many afd_filter iterations -> quantise; with AFD_F32 the whole call
+ * is bit-identical to afd_filter_out.  Bytes moved per voxel-iteration:
+ * 2 * element size / T.  Uses one cube of context scratch in the storage
+ * format (plus two float32 cubes when nx * element size is not a multiple of
+ * 16 bytes, or K = +inf, where passes go through float32 scratch).
+ * Asynchronous. */
+afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage storage,
+                         float scale, int64_t nx, int64_t ny, int64_t nz,
+                         const float *spacing, float K, float dt, int n_iter,
+                         afd_conductance cond, int t_block);
+
 /* FP64 statistics of a float32 cube (noise level and conservation check).
  *   cube     DEVICE pointer to n floats.
  *   out4     DEVICE pointer to 4 doubles receiving, in this order:

@@ -49,6 +49,10 @@ def _load():
         "afd_filter_out": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_host": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_selftest_wait": ([vp, i64], c_int),
+        "afd_quantize": ([vp, vp, vp, i64, c_int, f32], c_int),
+        "afd_dequantize": ([vp, vp, vp, i64, c_int, f32], c_int),
+        "afd_filter_ex": ([vp, vp, vp, c_int, f32, i64, i64, i64, vp, f32, f32, c_int, c_int,
+                           c_int], c_int),
         "afd_filter_noalloc": ([vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int, vp], c_int),
         "afd_stats": ([vp, vp, i64, vp], c_int),
         "afd_noise_rms": ([vp, vp, i64, dp], c_int),
@@ -194,6 +198,63 @@ def afd_filter_host(ctx: Context, host_in: torch.Tensor, host_out: torch.Tensor,
                                 float(K), float(dt), int(n_iter), COND[conductance]),
            "afd_filter_host", ctx)
     return host_out
+
+
+STORAGE_DTYPE = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16,
+                 "i16": torch.int16}
+
+
+def _storage_tensor(t: torch.Tensor, storage: str, what: str):
+    if STORAGE_DTYPE[storage] != t.dtype or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s: expected a contiguous %s CUDA tensor for storage %r"
+                         % (what, STORAGE_DTYPE[storage], storage))
+
+
+def afd_quantize(ctx: Context, cube: torch.Tensor, out: torch.Tensor, storage: str,
+                 scale: float) -> torch.Tensor:
+    """float32 CUDA tensor -> 2-byte storage tensor (float16, bfloat16 or
+    int16 counts of scale/1024), on the current stream."""
+    if cube.dtype != torch.float32 or not cube.is_cuda or not cube.is_contiguous():
+        raise ValueError("afd_quantize takes a contiguous float32 CUDA tensor")
+    _storage_tensor(out, storage, "afd_quantize")
+    if out.numel() != cube.numel():
+        raise ValueError("sizes differ")
+    _use_current_stream(ctx, cube)
+    _check(_lib.afd_quantize(ctx.handle, ctypes.c_void_p(cube.data_ptr()),
+                             ctypes.c_void_p(out.data_ptr()), cube.numel(), STORAGE[storage],
+                             float(scale)), "afd_quantize", ctx)
+    return out
+
+
+def afd_dequantize(ctx: Context, q: torch.Tensor, out: torch.Tensor, storage: str,
+                   scale: float) -> torch.Tensor:
+    """2-byte storage tensor -> float32 CUDA tensor, on the current stream."""
+    _storage_tensor(q, storage, "afd_dequantize")
+    if out.dtype != torch.float32 or not out.is_cuda or out.numel() != q.numel():
+        raise ValueError("out must be a float32 CUDA tensor of the same size")
+    _use_current_stream(ctx, q)
+    _check(_lib.afd_dequantize(ctx.handle, ctypes.c_void_p(q.data_ptr()),
+                               ctypes.c_void_p(out.data_ptr()), q.numel(), STORAGE[storage],
+                               float(scale)), "afd_dequantize", ctx)
+    return out
+
+
+def afd_filter_ex(ctx: Context, cube_in: torch.Tensor, cube_out: torch.Tensor, storage: str,
+                  scale: float, K: float, dt: float, n_iter: int, conductance: str = "rational",
+                  spacing=None, t_block: int = 0) -> torch.Tensor:
+    """Filter a cube stored as float32, float16, bfloat16 or int16 counts,
+    T = t_block iterations per pass; K in value units."""
+    _storage_tensor(cube_in, storage, "afd_filter_ex")
+    _storage_tensor(cube_out, storage, "afd_filter_ex")
+    if cube_in.shape != cube_out.shape:
+        raise ValueError("input and output shapes differ")
+    p_in, nx, ny, nz = _cube_args(cube_in)
+    p_out, _, _, _ = _cube_args(cube_out)
+    _use_current_stream(ctx, cube_in)
+    _check(_lib.afd_filter_ex(ctx.handle, p_in, p_out, STORAGE[storage], float(scale), nx, ny, nz,
+                              _spacing(spacing), float(K), float(dt), int(n_iter),
+                              COND[conductance], int(t_block)), "afd_filter_ex", ctx)
+    return cube_out
 
 
 NOALLOC_MAX_VOXELS = 8388608

@@ -17,6 +17,7 @@
 
 #include "../../include/afd.h"
 #include "afd_internal.h"
+#include "afd_store.cuh"
 
 struct afd_ctx {
     int device = 0;
@@ -30,6 +31,11 @@ struct afd_ctx {
     size_t scratch_bytes = 0;
     float *stage = nullptr;      // device copy for afd_filter_host
     size_t stage_bytes = 0;
+    float *lp_scratch = nullptr; // ping-pong partner of afd_filter_ex (any storage)
+    size_t lp_scratch_bytes = 0;
+    float *fb_scratch = nullptr; // float32 pair for the afd_filter_ex fallback
+    size_t fb_scratch_bytes = 0;
+    bool tb_ready[4][9] = {};    // tb_prepare done, per storage kind and depth
     double *d_part = nullptr;    // stats partials
     int part_blocks = 0;
     double *d_out4 = nullptr;    // stats result (device)
@@ -132,8 +138,7 @@ bool params_ok(const float *spacing, float K, float dt, int n_iter, afd_conducta
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
 
-afd_status encode_plane_map(afd_ctx *ctx, CUtensorMap *map, const float *ptr, int nx, int ny,
-                            int nz)
+bool resolve_encode()
 {
     std::call_once(g_encode_once, [] {
         cudaDriverEntryPointQueryResult q;
@@ -143,7 +148,13 @@ afd_status encode_plane_map(afd_ctx *ctx, CUtensorMap *map, const float *ptr, in
             q == cudaDriverEntryPointSuccess)
             g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     });
-    if (!g_encode) {
+    return g_encode != nullptr;
+}
+
+afd_status encode_plane_map(afd_ctx *ctx, CUtensorMap *map, const float *ptr, int nx, int ny,
+                            int nz)
+{
+    if (!resolve_encode()) {
         std::snprintf(ctx->errstr, sizeof(ctx->errstr), "cuTensorMapEncodeTiled unavailable");
         return AFD_ECUDA;
     }
@@ -266,6 +277,77 @@ afd_status filter_device(afd_ctx *ctx, const float *in, float *out, int64_t nx, 
     return AFD_OK;
 }
 
+
+bool pow2_scale_ok(float scale)
+{
+    if (!(scale > 0.0f) || !std::isfinite(scale))
+        return false;
+    int e = 0;
+    return std::frexp(static_cast<double>(scale), &e) == 0.5;
+}
+
+bool storage_ok(int s) { return s == AFD_F32 || s == AFD_F16 || s == AFD_BF16 || s == AFD_I16FIX; }
+
+// Encode a 3-D TMA map over a cube of storage kind S for the temporally
+// blocked kernel of depth T.
+afd_status encode_tb_map(afd_ctx *ctx, CUtensorMap *map, const void *ptr, int S, int T, int nx,
+                         int ny, int nz)
+{
+    if (!resolve_encode()) {
+        std::snprintf(ctx->errstr, sizeof(ctx->errstr), "cuTensorMapEncodeTiled unavailable");
+        return AFD_ECUDA;
+    }
+    const afd::TbShape sh = afd::tb_shape(S, T);
+    const cuuint64_t es = static_cast<cuuint64_t>(afd::store_bytes(S));
+    const cuuint64_t dims[3] = {static_cast<cuuint64_t>(nx), static_cast<cuuint64_t>(ny),
+                                static_cast<cuuint64_t>(nz)};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(nx) * es,
+                                   static_cast<cuuint64_t>(nx) * static_cast<cuuint64_t>(ny) * es};
+    const cuuint32_t box[3] = {static_cast<cuuint32_t>(sh.box_w), static_cast<cuuint32_t>(sh.box_h),
+                               1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(map,
+                          S == AFD_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                       : CU_TENSOR_MAP_DATA_TYPE_UINT16,
+                          3, const_cast<void *>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        std::snprintf(ctx->errstr, sizeof(ctx->errstr), "cuTensorMapEncodeTiled failed (%d)",
+                      static_cast<int>(r));
+        return AFD_ECUDA;
+    }
+    return AFD_OK;
+}
+
+// One pass of depth T without the temporally blocked kernel (layout it cannot
+// stage, or K = +inf): dequantise into float32 scratch, T float32
+// iterations, quantise.  The same arithmetic, so the same bits.
+afd_status fallback_pass(afd_ctx *ctx, int S, float units, const void *src, void *dst, int64_t nx,
+                         int64_t ny, int64_t nz, const float *spacing, float K, float dt, int T,
+                         afd_conductance cond)
+{
+    const int64_t n = nx * ny * nz;
+    const size_t fbytes = static_cast<size_t>(n) * sizeof(float);
+    if (S == AFD_F32)
+        return filter_device(ctx, static_cast<const float *>(src), static_cast<float *>(dst), nx,
+                             ny, nz, spacing, K, dt, T, cond);
+    afd_status st = ensure_buffer(ctx, &ctx->fb_scratch, &ctx->fb_scratch_bytes, 2 * fbytes);
+    if (st != AFD_OK)
+        return st;
+    float *a = ctx->fb_scratch, *b = ctx->fb_scratch + n;
+    cudaError_t e = afd::launch_dequantize(S, src, a, n, units, ctx->stream);
+    ctx->launches++;
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    st = filter_device(ctx, a, b, nx, ny, nz, spacing, K, dt, T, cond);
+    if (st != AFD_OK)
+        return st;
+    e = afd::launch_quantize(S, b, dst, n, units, ctx->stream);
+    ctx->launches++;
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+}
+
 afd_status stats_device(afd_ctx *ctx, const float *cube, int64_t n, double *out4)
 {
     cudaError_t e = afd::launch_stats(cube, n, ctx->d_part, ctx->part_blocks, out4, ctx->stream);
@@ -347,6 +429,10 @@ afd_status afd_destroy(afd_ctx *ctx)
         cudaFree(ctx->scratch);
     if (ctx->stage)
         cudaFree(ctx->stage);
+    if (ctx->lp_scratch)
+        cudaFree(ctx->lp_scratch);
+    if (ctx->fb_scratch)
+        cudaFree(ctx->fb_scratch);
     if (ctx->d_err)
         cudaFree(ctx->d_err);
     if (ctx->h_out4)
@@ -437,6 +523,159 @@ afd_status afd_filter_host(afd_ctx *ctx, const float *host_in, float *host_out, 
     if (e != cudaSuccess)
         return cuda_fail(ctx, e);
     return afd_sync(ctx);
+}
+
+afd_status afd_quantize(afd_ctx *ctx, const float *in, void *out, int64_t n, afd_storage storage,
+                        float scale)
+{
+    if (!ctx || !in || !out || n < 1 || !storage_ok(storage) || storage == AFD_F32 ||
+        !pow2_scale_ok(scale))
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    const float units = static_cast<float>(afd::store_units_per_value(storage, scale));
+    cudaError_t e = afd::launch_quantize(storage, in, out, n, units, ctx->stream);
+    ctx->launches++;
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+}
+
+afd_status afd_dequantize(afd_ctx *ctx, const void *in, float *out, int64_t n,
+                          afd_storage storage, float scale)
+{
+    if (!ctx || !in || !out || n < 1 || !storage_ok(storage) || storage == AFD_F32 ||
+        !pow2_scale_ok(scale))
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    const float units = static_cast<float>(afd::store_units_per_value(storage, scale));
+    cudaError_t e = afd::launch_dequantize(storage, in, out, n, units, ctx->stream);
+    ctx->launches++;
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+}
+
+afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage storage,
+                         float scale, int64_t nx, int64_t ny, int64_t nz, const float *spacing,
+                         float K, float dt, int n_iter, afd_conductance cond, int t_block)
+{
+    if (!ctx || !in || !out || !storage_ok(storage) || !dims_ok(nx, ny, nz) ||
+        !params_ok(spacing, K, dt, n_iter, cond))
+        return AFD_EINVAL;
+    if (storage == AFD_F32)
+        scale = 1.0f;
+    if (!pow2_scale_ok(scale))
+        return AFD_EINVAL;
+    if (t_block == 0)
+        t_block = (storage == AFD_F32) ? 2 : 4;
+    if (!afd::tb_depth_ok(t_block))
+        return AFD_EINVAL;
+    const int S = storage;
+    const int64_t n = nx * ny * nz;
+    const size_t bytes = static_cast<size_t>(n) * static_cast<size_t>(afd::store_bytes(S));
+    if (in != out) {
+        const char *a = static_cast<const char *>(in);
+        const char *b = static_cast<const char *>(out);
+        if (a < b + bytes && b < a + bytes)
+            return AFD_EINVAL;
+    }
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    cudaError_t e = cudaSuccess;
+    if (n_iter == 0 || K == 0.0f) {  // identity
+        if (in != out)
+            e = cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+    }
+    st = ensure_buffer(ctx, &ctx->lp_scratch, &ctx->lp_scratch_bytes, bytes);
+    if (st != AFD_OK)
+        return st;
+    void *scr = ctx->lp_scratch;
+    const double units_d = afd::store_units_per_value(S, scale);
+    const float units = static_cast<float>(units_d);
+    // K in storage units (exact: units is a power of two)
+    const float Ks = std::isinf(K) ? K : static_cast<float>(static_cast<double>(K) * units_d);
+    int kind = 0;
+    const afd::Coef k = afd::make_coef(spacing, Ks, dt, cond == AFD_COND_EXPONENTIAL, &kind);
+
+    // passes: n_iter / t_block of depth t_block, then the remainder as
+    // passes of depth 4, 2 and 1 (each at most t_block)
+    int npass = 0;
+    {
+        int left = n_iter, m = 0;
+        while (left >= t_block) {
+            ++m;
+            left -= t_block;
+        }
+        for (int d = 4; d >= 1; d >>= 1)
+            while (d <= t_block && left >= d) {
+                ++m;
+                left -= d;
+            }
+        npass = m;
+    }
+    auto depth_of = [&](int i) -> int {
+        const int full = n_iter / t_block;
+        if (i < full)
+            return t_block;
+        int left = n_iter - full * t_block, j = full;
+        for (int d = 4; d >= 1; d >>= 1)
+            while (d <= t_block && left >= d) {
+                if (j == i)
+                    return d;
+                ++j;
+                left -= d;
+            }
+        return 1;
+    };
+    const bool inplace = (in == out);
+    auto dst_of = [&](int i) -> void * {
+        if (inplace)
+            return (i & 1) ? out : scr;
+        return ((npass - 1 - i) & 1) ? scr : out;
+    };
+    auto src_of = [&](int i) -> const void * { return i == 0 ? in : dst_of(i - 1); };
+
+    const int es = afd::store_bytes(S);
+    const bool fits = ((nx * es) % 16 == 0) && (reinterpret_cast<uintptr_t>(in) & 15u) == 0 &&
+                      (reinterpret_cast<uintptr_t>(out) & 15u) == 0 && !std::isinf(K) &&
+                      (reinterpret_cast<uintptr_t>(scr) & 15u) == 0;
+    for (int i = 0; i < npass; ++i) {
+        const int T = depth_of(i);
+        if (fits) {
+            if (!ctx->tb_ready[S][T]) {
+                e = afd::tb_prepare(S, T);
+                if (e != cudaSuccess)
+                    return cuda_fail(ctx, e);
+                ctx->tb_ready[S][T] = true;
+            }
+            CUtensorMap map;
+            st = encode_tb_map(ctx, &map, src_of(i), S, T, static_cast<int>(nx),
+                               static_cast<int>(ny), static_cast<int>(nz));
+            if (st != AFD_OK)
+                return st;
+            const afd::TbPlan plan = afd::tb_plan(S, T, static_cast<int>(nx), static_cast<int>(ny),
+                                                  static_cast<int>(nz), ctx->sm_count, ctx->zc_hint);
+            e = afd::tb_launch(S, T, kind, map, dst_of(i), static_cast<int>(nx),
+                               static_cast<int>(ny), static_cast<int>(nz), k, plan, ctx->d_err,
+                               ctx->stream);
+            ctx->launches++;
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e);
+        } else {
+            st = fallback_pass(ctx, S, units, src_of(i), dst_of(i), nx, ny, nz, spacing, K, dt, T,
+                               cond);
+            if (st != AFD_OK)
+                return st;
+        }
+    }
+    if (dst_of(npass - 1) != out) {
+        e = cudaMemcpyAsync(out, dst_of(npass - 1), bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e);
+    }
+    return AFD_OK;
 }
 
 afd_status afd_stats(afd_ctx *ctx, const float *cube, int64_t n, double *out4)

@@ -42,6 +42,49 @@ cudaError_t launch_pm_stream(int cond, const CUtensorMap &tmap_in, float *out, i
                              int nz, const Coef &k, const StreamPlan &plan, int *err,
                              cudaStream_t stream);
 
+// ---- temporally blocked kernel (T iterations per pass, any storage) --------
+struct TbShape {
+    int tx, ty;          // interior tile
+    int box_w, box_h;    // TMA box (elements, rows)
+    int hx;              // TMA box starts at x0 - hx, y0 - T
+    int threads;         // threads per CTA
+    size_t smem;         // dynamic shared memory per CTA
+};
+
+struct TbPlan {
+    int tiles_x, tiles_y, zc;
+    int64_t ntiles;
+    int grid;
+};
+
+// Dispatch on storage kind S (StoreKind) and depth T in {1, 2, 4, 8}.
+bool tb_depth_ok(int T);
+cudaError_t tb_prepare(int S, int T);
+TbShape tb_shape(int S, int T);
+TbPlan tb_plan(int S, int T, int nx, int ny, int nz, int sm_count, int zc_hint);
+cudaError_t tb_launch(int S, int T, int cond, const CUtensorMap &tmap, void *out, int nx, int ny,
+                      int nz, const Coef &k, const TbPlan &plan, int *err, cudaStream_t stream);
+
+#define AFD_TB_DECL(n)                                                                           \
+    cudaError_t tb_prepare_##n(int T);                                                           \
+    TbShape tb_shape_##n(int T);                                                                 \
+    cudaError_t tb_launch_##n(int T, int cond, const CUtensorMap &tmap, void *out, int nx,       \
+                              int ny, int nz, const Coef &k, const TbPlan &plan, int *err,       \
+                              cudaStream_t stream);
+AFD_TB_DECL(f32)
+AFD_TB_DECL(f16)
+AFD_TB_DECL(bf16)
+AFD_TB_DECL(i16)
+#undef AFD_TB_DECL
+
+// ---- storage conversion (a2 quantise, a7 dequantise) -----------------------
+// units = storage units per value unit (a power of two); quantise computes
+// store(v * units), dequantise load(q) / units, elementwise over n values.
+cudaError_t launch_quantize(int S, const float *in, void *out, int64_t n, float units,
+                            cudaStream_t stream);
+cudaError_t launch_dequantize(int S, const void *in, float *out, int64_t n, float units,
+                              cudaStream_t stream);
+
 // ---- FP64 statistics -------------------------------------------------------
 constexpr int kStatsThreads = 256;
 // partials: 4 doubles per block; out4: sum, sum sq, negative sum sq, count
