@@ -288,23 +288,32 @@ bool pow2_scale_ok(float scale)
 
 bool storage_ok(int s) { return s == AFD_F32 || s == AFD_F16 || s == AFD_BF16 || s == AFD_I16FIX; }
 
+// Encode a 3-D TMA map over a cube of storage kind S with the given box.
+afd_status encode_box_map(afd_ctx *ctx, CUtensorMap *map, const void *ptr, int S, int box_w,
+                          int box_h, int nx, int ny, int nz);
+
 // Encode a 3-D TMA map over a cube of storage kind S for the temporally
 // blocked kernel of depth T.
 afd_status encode_tb_map(afd_ctx *ctx, CUtensorMap *map, const void *ptr, int S, int T, int nx,
                          int ny, int nz)
 {
+    const afd::TbShape sh = afd::tb_shape(S, T);
+    return encode_box_map(ctx, map, ptr, S, sh.box_w, sh.box_h, nx, ny, nz);
+}
+
+afd_status encode_box_map(afd_ctx *ctx, CUtensorMap *map, const void *ptr, int S, int box_w,
+                          int box_h, int nx, int ny, int nz)
+{
     if (!resolve_encode()) {
         std::snprintf(ctx->errstr, sizeof(ctx->errstr), "cuTensorMapEncodeTiled unavailable");
         return AFD_ECUDA;
     }
-    const afd::TbShape sh = afd::tb_shape(S, T);
     const cuuint64_t es = static_cast<cuuint64_t>(afd::store_bytes(S));
     const cuuint64_t dims[3] = {static_cast<cuuint64_t>(nx), static_cast<cuuint64_t>(ny),
                                 static_cast<cuuint64_t>(nz)};
     const cuuint64_t strides[2] = {static_cast<cuuint64_t>(nx) * es,
                                    static_cast<cuuint64_t>(nx) * static_cast<cuuint64_t>(ny) * es};
-    const cuuint32_t box[3] = {static_cast<cuuint32_t>(sh.box_w), static_cast<cuuint32_t>(sh.box_h),
-                               1};
+    const cuuint32_t box[3] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = g_encode(map,
                           S == AFD_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -643,7 +652,35 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
                       (reinterpret_cast<uintptr_t>(scr) & 15u) == 0;
     for (int i = 0; i < npass; ++i) {
         const int T = depth_of(i);
-        if (fits) {
+        if (fits && T == 1) {
+            // depth 1: the barrier-free streaming kernel, on the stored format
+            if (ctx->stream_bps == 0) {
+                e = afd::pm_stream_prepare();
+                if (e == cudaSuccess)
+                    e = afd::pm_stream_occupancy(&ctx->stream_bps);
+                if (e != cudaSuccess)
+                    return cuda_fail(ctx, e);
+                if (ctx->stream_bps < 1)
+                    ctx->stream_bps = 1;
+            }
+            int bw = 0, bh = 0, hx = 0;
+            afd::pm_stream_box(S, &bw, &bh, &hx);
+            CUtensorMap map;
+            st = encode_box_map(ctx, &map, src_of(i), S, bw, bh, static_cast<int>(nx),
+                                static_cast<int>(ny), static_cast<int>(nz));
+            if (st != AFD_OK)
+                return st;
+            const afd::StreamPlan plan =
+                afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
+                                    static_cast<int>(nz), ctx->sm_count, ctx->stream_bps,
+                                    ctx->zc_hint);
+            e = afd::launch_pm_stream_s(S, kind, map, dst_of(i), static_cast<int>(nx),
+                                        static_cast<int>(ny), static_cast<int>(nz), k, plan,
+                                        ctx->d_err, ctx->stream);
+            ctx->launches++;
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e);
+        } else if (fits) {
             if (!ctx->tb_ready[S][T]) {
                 e = afd::tb_prepare(S, T);
                 if (e != cudaSuccess)

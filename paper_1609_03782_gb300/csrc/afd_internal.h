@@ -41,6 +41,11 @@ StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_s
 cudaError_t launch_pm_stream(int cond, const CUtensorMap &tmap_in, float *out, int nx, int ny,
                              int nz, const Coef &k, const StreamPlan &plan, int *err,
                              cudaStream_t stream);
+// Any storage kind (StoreKind); the map's box is pm_stream_box(S, ...).
+cudaError_t launch_pm_stream_s(int S, int cond, const CUtensorMap &tmap_in, void *out, int nx,
+                               int ny, int nz, const Coef &k, const StreamPlan &plan, int *err,
+                               cudaStream_t stream);
+void pm_stream_box(int S, int *box_w, int *box_h, int *hx);
 
 // ---- temporally blocked kernel (T iterations per pass, any storage) --------
 struct TbShape {

@@ -24,24 +24,39 @@
 //     so results are bit-identical to the one-voxel-per-thread kernel).
 //   * Tiles that touch no cube face take a path without boundary selects.
 //   * Results go straight to global memory with 16-byte stores.
-// Requirements checked by the host: nx % 4 == 0, 16-byte aligned pointers.
-// Every mbarrier wait is bounded (afd_ptx.cuh).
+//   * The cube may be stored as float32 or in a 2-byte format
+//     (afd_store.cuh): planes are converted to float32 as they are read from
+//     the ring and rounded back on store, so a launch on a 2-byte cube is one
+//     depth-1 pass of afd_filter_ex.
+// Requirements checked by the host: nx * element size a multiple of 16
+// bytes, 16-byte aligned pointers.  Every mbarrier wait is bounded
+// (afd_ptx.cuh).
 #include "afd_internal.h"
 #include "afd_ptx.cuh"
+#include "afd_store.cuh"
 
 namespace afd {
 namespace {
 
 constexpr int TX = kStreamTX;
 constexpr int TY = kStreamTY;
-constexpr int PX = TX + 8;                                 // floats per slot row
 constexpr int PY = TY + 2;                                 // rows per slot
-constexpr uint32_t BOX_BYTES = PX * PY * sizeof(float);    // one TMA box
-constexpr int SLOT_BYTES = (BOX_BYTES + 127) / 128 * 128;  // 128-B aligned slots
-constexpr int SLOT_FLOATS = SLOT_BYTES / 4;
 constexpr uint32_t NSLOT = kStreamSlots;                   // power of two
+
+// Slot geometry per storage kind: the x halo is 16 bytes (4 floats or 8
+// 2-byte elements) each side so that the TMA x coordinate stays aligned.
+template <int S>
+struct Slot {
+    static constexpr int ES = Store<S>::bytes;
+    static constexpr int HX = 16 / ES;
+    static constexpr int PX = TX + 2 * HX;                      // elements per row
+    static constexpr uint32_t BOX_BYTES = PX * PY * ES;         // one TMA box
+    static constexpr int BYTES = (BOX_BYTES + 127) / 128 * 128;  // 128-B aligned
+};
+constexpr int SLOT_BYTES_MAX = Slot<STORE_F32>::BYTES;
 constexpr int NCW = kStreamConsumerWarps;
 static_assert(TX == 16 * 4 && TY == 2 * 16 && NCW * 32 == 256, "thread mapping");
+static_assert(Slot<STORE_F16>::BYTES <= SLOT_BYTES_MAX, "slot sizes");
 static_assert((NSLOT & (NSLOT - 1)) == 0, "ring size must be a power of two");
 
 struct TileCoord {
@@ -86,12 +101,44 @@ __device__ __forceinline__ Q q_flux(Q d, f2_t A2, f2_t B2, f2_t Z2)
     return {face_flux2<C>(d.a, A2, B2, Z2), face_flux2<C>(d.b, A2, B2, Z2)};
 }
 
-__device__ __forceinline__ void stg_q(float *p, Q v)
+// Four stored elements at element offset `off` of a slot -> float32 quad.
+template <int S>
+__device__ __forceinline__ Q lds_qs(const unsigned char *slot, int off)
+{
+    if constexpr (S == STORE_F32) {
+        return lds_q(reinterpret_cast<const float *>(slot) + off);
+    } else {
+        typedef typename Store<S>::T E;
+        const uint2 w = *reinterpret_cast<const uint2 *>(slot + off * 2);
+        return {f2_pack(Store<S>::load(static_cast<E>(w.x & 0xffffu)),
+                        Store<S>::load(static_cast<E>(w.x >> 16))),
+                f2_pack(Store<S>::load(static_cast<E>(w.y & 0xffffu)),
+                        Store<S>::load(static_cast<E>(w.y >> 16)))};
+    }
+}
+
+template <int S>
+__device__ __forceinline__ float lds_s(const unsigned char *slot, int off)
+{
+    typedef typename Store<S>::T E;
+    return Store<S>::load(reinterpret_cast<const E *>(slot)[off]);
+}
+
+template <int S>
+__device__ __forceinline__ void stg_q(typename Store<S>::T *p, Q v)
 {
     float4 o;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(v.a));
     asm("mov.b64 {%0, %1}, %2;" : "=f"(o.z), "=f"(o.w) : "l"(v.b));
-    *reinterpret_cast<float4 *>(p) = o;
+    if constexpr (S == STORE_F32) {
+        *reinterpret_cast<float4 *>(p) = o;
+    } else {
+        const unsigned u0 = static_cast<unsigned short>(Store<S>::store(o.x));
+        const unsigned u1 = static_cast<unsigned short>(Store<S>::store(o.y));
+        const unsigned u2 = static_cast<unsigned short>(Store<S>::store(o.z));
+        const unsigned u3 = static_cast<unsigned short>(Store<S>::store(o.w));
+        *reinterpret_cast<uint2 *>(p) = make_uint2(u0 | (u1 << 16), u2 | (u3 << 16));
+    }
 }
 
 struct Packed {
@@ -115,17 +162,18 @@ __device__ __forceinline__ Q x_sums(Q c, float xl, float f4, const Packed &k)
     return {f2_sub(f12, f01), f2_sub(f34, f23)};
 }
 
-template <int C>
+template <int S, int C>
 __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
-    pm_step_stream(const __grid_constant__ CUtensorMap tmap, float *__restrict__ out, int nx,
-                   int ny, int nz, int tiles_x, int tiles_y, int zc, int64_t ntiles, Coef kc,
-                   int *err)
+    pm_step_stream(const __grid_constant__ CUtensorMap tmap, typename Store<S>::T *__restrict__ out,
+                   int nx, int ny, int nz, int tiles_x, int tiles_y, int zc, int64_t ntiles,
+                   Coef kc, int *err)
 {
+    typedef Slot<S> SL;
     extern __shared__ unsigned char smem_raw[];
     const uint32_t base = smem_u32(smem_raw);
     unsigned char *smem = smem_raw + ((128u - (base & 127u)) & 127u);
-    float *slots = reinterpret_cast<float *>(smem);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + NSLOT * SLOT_BYTES);
+    unsigned char *slots = smem;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + NSLOT * SLOT_BYTES_MAX);
     uint64_t *empty = full + NSLOT;
 
     const int warp = threadIdx.x >> 5;
@@ -150,8 +198,8 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
                     const uint32_t use = kk / NSLOT;
                     if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1u, err, kErrWaitEmpty))
                         return;
-                    mbar_arrive_expect_tx(&full[slot], BOX_BYTES);
-                    tma_load_3d(slots + slot * SLOT_FLOATS, &tmap, tc.x0 - 4, tc.y0 - 1,
+                    mbar_arrive_expect_tx(&full[slot], SL::BOX_BYTES);
+                    tma_load_3d(slots + slot * SLOT_BYTES_MAX, &tmap, tc.x0 - SL::HX, tc.y0 - 1,
                                 tc.zlo + j, &full[slot]);
                 }
             }
@@ -171,8 +219,8 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
     const int qx = threadIdx.x & 15;
     const int ry = threadIdx.x >> 4;
     const int r0 = 1 + 2 * ry;                      // slot row of the first row
-    const int cen0 = r0 * PX + 4 + 4 * qx;          // quad of row 0 in a slot
-    const int cen1 = cen0 + PX;                     // quad of row 1
+    const int cen0 = r0 * SL::PX + SL::HX + 4 * qx;  // quad of row 0 in a slot (elements)
+    const int cen1 = cen0 + SL::PX;                  // quad of row 1
     uint32_t kk = 0;
 
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -186,10 +234,10 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
                           (tc.y0 + TY >= ny);
         const uint32_t kbase = kk;
         const int64_t row_stride = nx;
-        float *out0 = out + (static_cast<int64_t>(ya) * nx + x);
+        typename Store<S>::T *out0 = out + (static_cast<int64_t>(ya) * nx + x);
 
 #define RING(z) (kbase + static_cast<uint32_t>((z) - tc.zlo))
-#define SLOT_PTR(r) (slots + ((r) & (NSLOT - 1)) * SLOT_FLOATS)
+#define SLOT_PTR(r) (slots + ((r) & (NSLOT - 1)) * SLOT_BYTES_MAX)
 #define WAIT_FULL(r)                                                                     \
     if (!mbar_wait(&full[(r) & (NSLOT - 1)], ((r) / NSLOT) & 1u, err, kErrWaitFull))      \
         return;
@@ -206,18 +254,18 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
             if (tc.z0 > 0) {
                 const uint32_t rb = RING(tc.z0 - 1);
                 WAIT_FULL(rb);
-                const Q p0 = lds_q(SLOT_PTR(rb) + cen0);
-                const Q p1 = lds_q(SLOT_PTR(rb) + cen1);
+                const Q p0 = lds_qs<S>(SLOT_PTR(rb), cen0);
+                const Q p1 = lds_qs<S>(SLOT_PTR(rb), cen1);
                 WAIT_FULL(rz);
-                cur0 = lds_q(SLOT_PTR(rz) + cen0);
-                cur1 = lds_q(SLOT_PTR(rz) + cen1);
+                cur0 = lds_qs<S>(SLOT_PTR(rz), cen0);
+                cur1 = lds_qs<S>(SLOT_PTR(rz), cen1);
                 fb0 = q_flux<C>(q_sub(cur0, p0), k.az, k.bz, k.z);
                 fb1 = q_flux<C>(q_sub(cur1, p1), k.az, k.bz, k.z);
                 RELEASE(rb);
             } else {
                 WAIT_FULL(rz);
-                cur0 = lds_q(SLOT_PTR(rz) + cen0);
-                cur1 = lds_q(SLOT_PTR(rz) + cen1);
+                cur0 = lds_qs<S>(SLOT_PTR(rz), cen0);
+                cur1 = lds_qs<S>(SLOT_PTR(rz), cen1);
                 fb0 = q_flux<C>(q_sub(cur0, cur0), k.az, k.bz, k.z);  // zero flux at z = 0
                 fb1 = q_flux<C>(q_sub(cur1, cur1), k.az, k.bz, k.z);
             }
@@ -225,14 +273,14 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
 
         for (int z = tc.z0; z < tc.z1; ++z) {
             const uint32_t rc = RING(z);
-            const float *s = SLOT_PTR(rc);
+            const unsigned char *s = SLOT_PTR(rc);
             // ---- z: the plane above and the flux through the upper face
             Q n0, n1, fa0, fa1;
             if (z + 1 < nz) {
                 const uint32_t rn = RING(z + 1);
                 WAIT_FULL(rn);
-                n0 = lds_q(SLOT_PTR(rn) + cen0);
-                n1 = lds_q(SLOT_PTR(rn) + cen1);
+                n0 = lds_qs<S>(SLOT_PTR(rn), cen0);
+                n1 = lds_qs<S>(SLOT_PTR(rn), cen1);
             } else {
                 n0 = cur0;  // zero flux at z = nz-1
                 n1 = cur1;
@@ -241,11 +289,11 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
             fa1 = q_flux<C>(q_sub(n1, cur1), k.az, k.bz, k.z);
 
             // ---- neighbours in the plane (own value across a cube face)
-            Q dn = lds_q(s + cen0 - PX);
-            Q up = lds_q(s + cen1 + PX);
+            Q dn = lds_qs<S>(s, cen0 - SL::PX);
+            Q up = lds_qs<S>(s, cen1 + SL::PX);
             Q mid = cur1;
-            float xl0 = s[cen0 - 1], xr0 = s[cen0 + 4];
-            float xl1 = s[cen1 - 1], xr1 = s[cen1 + 4];
+            float xl0 = lds_s<S>(s, cen0 - 1), xr0 = lds_s<S>(s, cen0 + 4);
+            float xl1 = lds_s<S>(s, cen1 - 1), xr1 = lds_s<S>(s, cen1 + 4);
             if (edge) {
                 float c0a = f2_lo(cur0.a), c3a = f2_hi(cur0.b);
                 float c0b = f2_lo(cur1.a), c3b = f2_hi(cur1.b);
@@ -281,11 +329,11 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
                           pm_update2(cur0.b, sx0.b, f2_sub(fmid.b, fdn.b), f2_sub(fa0.b, fb0.b))};
             const Q o1 = {pm_update2(cur1.a, sx1.a, f2_sub(fup.a, fmid.a), f2_sub(fa1.a, fb1.a)),
                           pm_update2(cur1.b, sx1.b, f2_sub(fup.b, fmid.b), f2_sub(fa1.b, fb1.b))};
-            float *po = out0 + static_cast<int64_t>(z) * ny * row_stride;
+            typename Store<S>::T *po = out0 + static_cast<int64_t>(z) * ny * row_stride;
             if (act0)
-                stg_q(po, o0);
+                stg_q<S>(po, o0);
             if (act1)
-                stg_q(po + row_stride, o1);
+                stg_q<S>(po + row_stride, o1);
 
             RELEASE(rc);
             cur0 = n0;
@@ -307,36 +355,59 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
 
 size_t pm_stream_smem_bytes()
 {
-    return static_cast<size_t>(NSLOT) * SLOT_BYTES + 2 * NSLOT * sizeof(uint64_t) + 128;
+    return static_cast<size_t>(NSLOT) * SLOT_BYTES_MAX + 2 * NSLOT * sizeof(uint64_t) + 128;
 }
+
+void pm_stream_box(int S, int *box_w, int *box_h, int *hx)
+{
+    const int es = S == STORE_F32 ? 4 : 2;
+    *hx = 16 / es;
+    *box_w = TX + 2 * *hx;
+    *box_h = PY;
+}
+
+namespace {
+template <int S, int C>
+cudaError_t stream_attr()
+{
+    return cudaFuncSetAttribute(pm_step_stream<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(pm_stream_smem_bytes()));
+}
+template <int S>
+cudaError_t stream_attr_all()
+{
+    cudaError_t e = stream_attr<S, COND_EXP>();
+    if (e == cudaSuccess)
+        e = stream_attr<S, COND_RAT>();
+    if (e == cudaSuccess)
+        e = stream_attr<S, COND_LIN>();
+    return e;
+}
+}  // namespace
 
 cudaError_t pm_stream_prepare()
 {
-    const int smem = static_cast<int>(pm_stream_smem_bytes());
-    cudaError_t e;
-    e = cudaFuncSetAttribute(pm_step_stream<COND_EXP>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess)
-        return e;
-    e = cudaFuncSetAttribute(pm_step_stream<COND_RAT>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess)
-        return e;
-    return cudaFuncSetAttribute(pm_step_stream<COND_LIN>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = stream_attr_all<STORE_F32>();
+    if (e == cudaSuccess)
+        e = stream_attr_all<STORE_F16>();
+    if (e == cudaSuccess)
+        e = stream_attr_all<STORE_BF16>();
+    if (e == cudaSuccess)
+        e = stream_attr_all<STORE_I16>();
+    return e;
 }
 
 cudaError_t pm_stream_occupancy(int *blocks_per_sm)
 {
     int a = 0, b = 0, c = 0;
     const size_t smem = pm_stream_smem_bytes();
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, pm_step_stream<COND_EXP>,
-                                                                  kStreamThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &a, pm_step_stream<STORE_F32, COND_EXP>, kStreamThreads, smem);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pm_step_stream<COND_RAT>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pm_step_stream<STORE_F32, COND_RAT>,
                                                           kStreamThreads, smem);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, pm_step_stream<COND_LIN>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, pm_step_stream<STORE_F16, COND_RAT>,
                                                           kStreamThreads, smem);
     *blocks_per_sm = min(a, min(b, c));
     return e;
@@ -381,26 +452,49 @@ StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_s
     return p;
 }
 
+namespace {
+template <int S, int C>
+cudaError_t stream_launch(const CUtensorMap &tmap, void *out, int nx, int ny, int nz,
+                          const Coef &k, const StreamPlan &plan, int *err, cudaStream_t stream)
+{
+    pm_step_stream<S, C><<<plan.grid, kStreamThreads, pm_stream_smem_bytes(), stream>>>(
+        tmap, static_cast<typename Store<S>::T *>(out), nx, ny, nz, plan.tiles_x, plan.tiles_y,
+        plan.zc, plan.ntiles, k, err);
+    return cudaGetLastError();
+}
+template <int S>
+cudaError_t stream_launch_c(int cond, const CUtensorMap &tmap, void *out, int nx, int ny, int nz,
+                            const Coef &k, const StreamPlan &plan, int *err, cudaStream_t stream)
+{
+    switch (cond) {
+    case COND_EXP: return stream_launch<S, COND_EXP>(tmap, out, nx, ny, nz, k, plan, err, stream);
+    case COND_RAT: return stream_launch<S, COND_RAT>(tmap, out, nx, ny, nz, k, plan, err, stream);
+    default: return stream_launch<S, COND_LIN>(tmap, out, nx, ny, nz, k, plan, err, stream);
+    }
+}
+}  // namespace
+
+cudaError_t launch_pm_stream_s(int S, int cond, const CUtensorMap &tmap_in, void *out, int nx,
+                               int ny, int nz, const Coef &k, const StreamPlan &plan, int *err,
+                               cudaStream_t stream)
+{
+    switch (S) {
+    case STORE_F32:
+        return stream_launch_c<STORE_F32>(cond, tmap_in, out, nx, ny, nz, k, plan, err, stream);
+    case STORE_F16:
+        return stream_launch_c<STORE_F16>(cond, tmap_in, out, nx, ny, nz, k, plan, err, stream);
+    case STORE_BF16:
+        return stream_launch_c<STORE_BF16>(cond, tmap_in, out, nx, ny, nz, k, plan, err, stream);
+    default:
+        return stream_launch_c<STORE_I16>(cond, tmap_in, out, nx, ny, nz, k, plan, err, stream);
+    }
+}
+
 cudaError_t launch_pm_stream(int cond, const CUtensorMap &tmap_in, float *out, int nx, int ny,
                              int nz, const Coef &k, const StreamPlan &plan, int *err,
                              cudaStream_t stream)
 {
-    const size_t smem = pm_stream_smem_bytes();
-    switch (cond) {
-    case COND_EXP:
-        pm_step_stream<COND_EXP><<<plan.grid, kStreamThreads, smem, stream>>>(
-            tmap_in, out, nx, ny, nz, plan.tiles_x, plan.tiles_y, plan.zc, plan.ntiles, k, err);
-        break;
-    case COND_RAT:
-        pm_step_stream<COND_RAT><<<plan.grid, kStreamThreads, smem, stream>>>(
-            tmap_in, out, nx, ny, nz, plan.tiles_x, plan.tiles_y, plan.zc, plan.ntiles, k, err);
-        break;
-    default:
-        pm_step_stream<COND_LIN><<<plan.grid, kStreamThreads, smem, stream>>>(
-            tmap_in, out, nx, ny, nz, plan.tiles_x, plan.tiles_y, plan.zc, plan.ntiles, k, err);
-        break;
-    }
-    return cudaGetLastError();
+    return launch_pm_stream_s(STORE_F32, cond, tmap_in, out, nx, ny, nz, k, plan, err, stream);
 }
 
 }  // namespace afd

@@ -54,6 +54,7 @@ struct Geom {
     static constexpr int BW = TX + 2 * HC + 8;  // stage plane row: x0-HC-4 .. x0+TX+HC+3
     static constexpr int BH = TY + 2 * T + 2;   // stage plane rows: y0-T-1 .. y0+TY+T
     static constexpr int BFLOATS = BW * BH;
+    static constexpr int MIN_BLOCKS = (T <= 2) ? 2 : 1;  // CTAs per SM to fit
     static_assert(BW % 4 == 0, "16-byte rows");
 };
 
@@ -160,7 +161,7 @@ __device__ __forceinline__ Q x_sums(Q c, float xl, float f4, const Packed &k)
 }
 
 template <int S, int T, int C>
-__global__ void __launch_bounds__(Geom<T>::THREADS, 1)
+__global__ void __launch_bounds__(Geom<T>::THREADS, Geom<T>::MIN_BLOCKS)
     pm_tb_kernel(const __grid_constant__ CUtensorMap tmap, typename Store<S>::T *__restrict__ out,
                  int nx, int ny, int nz, int tiles_x, int tiles_y, int zc, int64_t ntiles, Coef kc,
                  int *err)
@@ -267,11 +268,12 @@ __global__ void __launch_bounds__(Geom<T>::THREADS, 1)
         const bool out_a = out_x && (ya >= y0) && (ya < y0 + G::TY) && (ya < ny);
         const bool out_b = out_x && (yb >= y0) && (yb < y0 + G::TY) && (yb < ny);
 
-        Q cur[T + 1][2], fb[T + 1][2];
+        // per stage: the flux through the lower z face of its current plane
+        // (the current plane itself is re-read from the stage's input buffer)
+        Q fb[T + 1][2];
 #pragma unroll
-        for (int st = 0; st <= T; ++st) {
-            cur[st][0] = cur[st][1] = fb[st][0] = fb[st][1] = Q{0ull, 0ull};
-        }
+        for (int st = 0; st <= T; ++st)
+            fb[st][0] = fb[st][1] = Q{0ull, 0ull};
 
         for (int s = sbeg; s <= slast; ++s) {
             const int par = static_cast<int>(g & 1u);
@@ -299,27 +301,29 @@ __global__ void __launch_bounds__(Geom<T>::THREADS, 1)
 #pragma unroll
             for (int st = 1; st <= T; ++st) {
                 const int p = s - st;
+                // this stage's input plane p (stage st-1's output of the
+                // previous step) and its x/y neighbours
+                const float *B = bufs + ((st - 1) * 2 + (par ^ 1)) * G::BFLOATS;
+                const Q c0 = lds_q(B + ra), c1 = lds_q(B + rb);
                 Q nx2[2];
                 if (p + 1 < nz) {
                     nx2[0] = nxt[0];
                     nx2[1] = nxt[1];
                 } else {
-                    nx2[0] = cur[st][0];  // zero flux at z = nz-1
-                    nx2[1] = cur[st][1];
+                    nx2[0] = c0;  // zero flux at z = nz-1
+                    nx2[1] = c1;
                 }
-                const Q fa0 = q_flux<C>(q_sub(nx2[0], cur[st][0]), k.az, k.bz, k.z);
-                const Q fa1 = q_flux<C>(q_sub(nx2[1], cur[st][1]), k.az, k.bz, k.z);
+                const Q fa0 = q_flux<C>(q_sub(nx2[0], c0), k.az, k.bz, k.z);
+                const Q fa1 = q_flux<C>(q_sub(nx2[1], c1), k.az, k.bz, k.z);
                 const int pbeg = max(z0 - (T - st), 0);
                 const int pend = min(z1 + (T - st), nz);
                 Q o0 = nx2[0], o1 = nx2[1];
                 if (p >= pbeg && p < pend && ((need >> st) & 1u)) {
-                    const Q c0 = cur[st][0], c1 = cur[st][1];
                     Q fb0 = fb[st][0], fb1 = fb[st][1];
                     if (p == 0) {  // zero flux at z = 0
                         fb0 = q_flux<C>(q_sub(c0, c0), k.az, k.bz, k.z);
                         fb1 = q_flux<C>(q_sub(c1, c1), k.az, k.bz, k.z);
                     }
-                    const float *B = bufs + ((st - 1) * 2 + (par ^ 1)) * G::BFLOATS;
                     Q dn = lds_q(B + ra - G::BW);
                     Q up = lds_q(B + rb + G::BW);
                     Q mid = c1;
@@ -369,8 +373,6 @@ __global__ void __launch_bounds__(Geom<T>::THREADS, 1)
                 nxt[1] = o1;
                 fb[st][0] = fa0;
                 fb[st][1] = fa1;
-                cur[st][0] = nx2[0];
-                cur[st][1] = nx2[1];
             }
             asm volatile("bar.sync 1, %0;" ::"n"(G::NCONS) : "memory");
             ++g;

@@ -37,9 +37,9 @@ cudaError_t tb_launch(int S, int T, int cond, const CUtensorMap &tmap, void *out
     }
 }
 
-// One CTA per SM (the kernels use most of the shared memory).  The z-chunk
-// trades the pipeline's fill and drain (2T extra steps per chunk) against
-// keeping every SM busy over whole rounds of tiles.
+// CTAs per SM as the kernels are built (one or two).  The z-chunk trades the
+// pipeline's fill and drain (about T extra planes of work per chunk) against
+// keeping every CTA slot busy over whole rounds of tiles.
 TbPlan tb_plan(int S, int T, int nx, int ny, int nz, int sm_count, int zc_hint)
 {
     const TbShape sh = tb_shape(S, T);
@@ -47,7 +47,7 @@ TbPlan tb_plan(int S, int T, int nx, int ny, int nz, int sm_count, int zc_hint)
     p.tiles_x = (nx + sh.tx - 1) / sh.tx;
     p.tiles_y = (ny + sh.ty - 1) / sh.ty;
     const int64_t txy = static_cast<int64_t>(p.tiles_x) * p.tiles_y;
-    const int64_t gmax = sm_count > 0 ? sm_count : 1;
+    const int64_t gmax = static_cast<int64_t>(sm_count > 0 ? sm_count : 1) * (T <= 2 ? 2 : 1);
     int zc = zc_hint;
     if (zc <= 0) {
         const int cand[5] = {256, 128, 64, 32, 16};
@@ -58,7 +58,7 @@ TbPlan tb_plan(int S, int T, int nx, int ny, int nz, int sm_count, int zc_hint)
             const int64_t nt = txy * ((nz + c - 1) / c);
             const int64_t rounds = (nt + gmax - 1) / gmax;
             const double busy = static_cast<double>(nt) / static_cast<double>(rounds * gmax);
-            const double fill = static_cast<double>(c) / (c + 2.0 * T);
+            const double fill = static_cast<double>(c) / (c + static_cast<double>(T));
             const double score = busy * fill;
             if (score > best + 1e-9) {
                 best = score;
