@@ -227,6 +227,64 @@ afd_status afd_sync(afd_ctx *ctx);
  * without hanging a GPU. */
 afd_status afd_selftest_wait(afd_ctx *ctx, int64_t limit_ns);
 
+/* ---- resident batches (hundreds of uneven cutouts filtered together) ----
+ *
+ * A batch keeps `count` cubes resident in library-owned device memory (an
+ * input, a result and a scratch copy of each, rows padded to 16 bytes so the
+ * streaming kernel's TMA loads work for any nx).  afd_batch_filter filters all
+ * of them with one CUDA-graph launch: FP64 noise statistics of every cube,
+ * per-cube K and conductance coefficients computed on the device, then the
+ * n_iter passes, each one persistent launch over the tiles of all cubes.
+ * Each cube's result is bit-identical to afd_filter_out (float32) or
+ * afd_filter_ex with t_block 1 (2-byte storage) on that cube alone with the
+ * same K.  The paper motivates batches by the hundreds of galaxies a survey
+ * cube holds (Sec. 1). */
+typedef struct afd_batch afd_batch;
+
+/* dims: HOST array of 3*count int64 (nx, ny, nz of each cube).  storage and
+ * scale as for afd_filter_ex.  Allocates 3 x the padded cubes' bytes (plus
+ * small tables) and zeroes them.  AFD_EINVAL for bad sizes or scale,
+ * AFD_ENOMEM when the arena does not fit. */
+afd_status afd_batch_create(afd_ctx *ctx, afd_batch **out, int count, const int64_t *dims,
+                            afd_storage storage, float scale);
+
+/* Copy cube i (a DEVICE or HOST pointer to a dense nx*ny*nz array in the
+ * batch's storage format) into the batch's resident input.  Asynchronous on
+ * the context's stream. */
+afd_status afd_batch_set(afd_batch *b, int i, const void *cube);
+
+/* Copy the result of cube i out to a dense DEVICE or HOST array.
+ * Asynchronous on the context's stream (synchronise before reading host
+ * memory). */
+afd_status afd_batch_get(afd_batch *b, int i, void *cube);
+
+/* Filter every cube: n_iter >= 1 iterations from its resident input into its
+ * result.
+ *   K        HOST array of count floats: K[i] > 0 is cube i's K in value
+ *            units; K[i] < 0 asks for K = -K[i] * (noise rms of cube i),
+ *            the rms of its negative voxels in FP64 on the GPU (so -1.5 is
+ *            K = 1.5 sigma).  +inf (all cubes) gives the heat equation; 0,
+ *            NaN and a mix of finite and infinite values are AFD_EINVAL.
+ *   spacing, dt, cond  as for afd_filter (shared by the batch).
+ * The first call (and any call whose n_iter, dt, spacing, conductance or
+ * z-chunk differ from the previous one) captures a CUDA graph; later calls
+ * only copy K and launch it.  Asynchronous; waits for earlier work on the
+ * context's stream before reusing its K staging buffer. */
+afd_status afd_batch_filter(afd_batch *b, const float *K, const float *spacing, float dt,
+                            int n_iter, afd_conductance cond);
+
+/* The K each cube was filtered with in the last afd_batch_filter (value
+ * units), into a HOST array of count floats.  Synchronises the stream. */
+afd_status afd_batch_k(afd_batch *b, float *K_out);
+
+/* Tuning: z planes per tile of the batched streaming kernel (0 = 16).
+ * Results do not depend on it. */
+afd_status afd_batch_set_zchunk(afd_batch *b, int zc);
+
+/* Free the batch's device memory after the context's stream is idle.  NULL
+ * is accepted. */
+afd_status afd_batch_destroy(afd_batch *b);
+
 /* Largest cube afd_filter_noalloc accepts: 8,388,608 voxels, i.e. 32 MiB of
  * float32 scratch (for example 256 x 256 x 128). */
 #define AFD_NOALLOC_MAX_VOXELS 8388608

@@ -53,6 +53,13 @@ def _load():
         "afd_dequantize": ([vp, vp, vp, i64, c_int, f32], c_int),
         "afd_filter_ex": ([vp, vp, vp, c_int, f32, i64, i64, i64, vp, f32, f32, c_int, c_int,
                            c_int], c_int),
+        "afd_batch_create": ([vp, ctypes.POINTER(vp), c_int, vp, c_int, f32], c_int),
+        "afd_batch_set": ([vp, c_int, vp], c_int),
+        "afd_batch_get": ([vp, c_int, vp], c_int),
+        "afd_batch_filter": ([vp, vp, vp, f32, c_int, c_int], c_int),
+        "afd_batch_k": ([vp, vp], c_int),
+        "afd_batch_set_zchunk": ([vp, c_int], c_int),
+        "afd_batch_destroy": ([vp], c_int),
         "afd_filter_noalloc": ([vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int, vp], c_int),
         "afd_stats": ([vp, vp, i64, vp], c_int),
         "afd_noise_rms": ([vp, vp, i64, dp], c_int),
@@ -255,6 +262,93 @@ def afd_filter_ex(ctx: Context, cube_in: torch.Tensor, cube_out: torch.Tensor, s
                               _spacing(spacing), float(K), float(dt), int(n_iter),
                               COND[conductance], int(t_block)), "afd_filter_ex", ctx)
     return cube_out
+
+
+class Batch:
+    """A resident batch of cubes (afd_batch*).  `shapes` are (nz, ny, nx)."""
+
+    def __init__(self, ctx: Context, shapes, storage: str = "f32", scale: float = 1.0):
+        import numpy as _np
+        self.ctx = ctx
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        self.storage = storage
+        dims = _np.array([[s[2], s[1], s[0]] for s in self.shapes], dtype=_np.int64).ravel()
+        h = ctypes.c_void_p()
+        _check(_lib.afd_batch_create(ctx.handle, ctypes.byref(h), len(self.shapes),
+                                     ctypes.c_void_p(dims.ctypes.data), STORAGE[storage],
+                                     float(scale)), "afd_batch_create", ctx)
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            _lib.afd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def afd_batch_create(ctx: Context, shapes, storage: str = "f32", scale: float = 1.0) -> Batch:
+    return Batch(ctx, shapes, storage, scale)
+
+
+def afd_batch_set(b: Batch, i: int, cube: torch.Tensor) -> None:
+    """Copy cube i (CUDA or CPU tensor in the batch's storage dtype, shape
+    (nz, ny, nx)) into the batch; asynchronous on the current stream."""
+    if tuple(cube.shape) != b.shapes[i] or cube.dtype != STORAGE_DTYPE[b.storage]:
+        raise ValueError("cube %d must have shape %s and dtype %s"
+                         % (i, b.shapes[i], STORAGE_DTYPE[b.storage]))
+    if not cube.is_contiguous():
+        raise ValueError("cube must be contiguous")
+    _use_current_stream(b.ctx, cube if cube.is_cuda else None)
+    _check(_lib.afd_batch_set(b.handle, int(i), ctypes.c_void_p(cube.data_ptr())),
+           "afd_batch_set", b.ctx)
+
+
+def afd_batch_get(b: Batch, i: int, out: torch.Tensor) -> torch.Tensor:
+    if tuple(out.shape) != b.shapes[i] or out.dtype != STORAGE_DTYPE[b.storage]:
+        raise ValueError("out must have shape %s and dtype %s" % (b.shapes[i],
+                                                                  STORAGE_DTYPE[b.storage]))
+    if not out.is_contiguous():
+        raise ValueError("out must be contiguous")
+    _use_current_stream(b.ctx, out if out.is_cuda else None)
+    _check(_lib.afd_batch_get(b.handle, int(i), ctypes.c_void_p(out.data_ptr())),
+           "afd_batch_get", b.ctx)
+    return out
+
+
+def afd_batch_filter(b: Batch, K, dt: float, n_iter: int, conductance: str = "rational",
+                     spacing=None) -> None:
+    """K: sequence of per-cube K (> 0: value units; < 0: -K times the cube's
+    noise rms, measured on the GPU)."""
+    import numpy as _np
+    k = _np.ascontiguousarray(_np.asarray(K, dtype=_np.float32).reshape(-1))
+    if k.size != len(b.shapes):
+        raise ValueError("need one K per cube")
+    _use_current_stream(b.ctx)
+    _check(_lib.afd_batch_filter(b.handle, ctypes.c_void_p(k.ctypes.data), _spacing(spacing),
+                                 float(dt), int(n_iter), COND[conductance]),
+           "afd_batch_filter", b.ctx)
+
+
+def afd_batch_k(b: Batch):
+    import numpy as _np
+    out = _np.zeros(len(b.shapes), dtype=_np.float32)
+    _use_current_stream(b.ctx)
+    _check(_lib.afd_batch_k(b.handle, ctypes.c_void_p(out.ctypes.data)), "afd_batch_k", b.ctx)
+    return out
+
+
+def afd_batch_set_zchunk(b: Batch, zc: int) -> None:
+    _use_current_stream(b.ctx)
+    _check(_lib.afd_batch_set_zchunk(b.handle, int(zc)), "afd_batch_set_zchunk", b.ctx)
+
+
+def afd_batch_destroy(b: Batch) -> None:
+    b.close()
 
 
 NOALLOC_MAX_VOXELS = 8388608

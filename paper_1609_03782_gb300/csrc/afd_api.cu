@@ -16,35 +16,11 @@
 #include <cuda_runtime.h>
 
 #include "../../include/afd.h"
+#include "afd_ctx.h"
 #include "afd_internal.h"
 #include "afd_store.cuh"
 
-struct afd_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int sm_count = 0;
-    int stream_bps = 0;          // streaming kernel CTAs per SM (occupancy)
-    int zc_hint = 0;             // streaming kernel z-chunk override (0 = auto)
-    afd_kernel kernel = AFD_KERNEL_AUTO;
-    int *d_err = nullptr;        // device error word (bounded-wait expiries)
-    float *scratch = nullptr;    // ping-pong partner buffer
-    size_t scratch_bytes = 0;
-    float *stage = nullptr;      // device copy for afd_filter_host
-    size_t stage_bytes = 0;
-    float *lp_scratch = nullptr; // ping-pong partner of afd_filter_ex (any storage)
-    size_t lp_scratch_bytes = 0;
-    float *fb_scratch = nullptr; // float32 pair for the afd_filter_ex fallback
-    size_t fb_scratch_bytes = 0;
-    bool tb_ready[4][9] = {};    // tb_prepare done, per storage kind and depth
-    double *d_part = nullptr;    // stats partials
-    int part_blocks = 0;
-    double *d_out4 = nullptr;    // stats result (device)
-    double *h_out4 = nullptr;    // stats result (pinned host)
-    uint64_t launches = 0;
-    char errstr[256] = {0};
-};
-
-namespace {
+namespace afd_host {
 
 // ---- fault injection: AFD_FAULT=alloc:N makes the N-th scratch allocation
 // of the process fail as if the device were out of memory (host side only).
@@ -304,6 +280,12 @@ afd_status encode_tb_map(afd_ctx *ctx, CUtensorMap *map, const void *ptr, int S,
 afd_status encode_box_map(afd_ctx *ctx, CUtensorMap *map, const void *ptr, int S, int box_w,
                           int box_h, int nx, int ny, int nz)
 {
+    return encode_pitched_map(ctx, map, ptr, S, box_w, box_h, nx, ny, nz, nx);
+}
+
+afd_status encode_pitched_map(afd_ctx *ctx, CUtensorMap *map, const void *ptr, int S, int box_w,
+                              int box_h, int nx, int ny, int nz, int64_t pitch)
+{
     if (!resolve_encode()) {
         std::snprintf(ctx->errstr, sizeof(ctx->errstr), "cuTensorMapEncodeTiled unavailable");
         return AFD_ECUDA;
@@ -311,8 +293,8 @@ afd_status encode_box_map(afd_ctx *ctx, CUtensorMap *map, const void *ptr, int S
     const cuuint64_t es = static_cast<cuuint64_t>(afd::store_bytes(S));
     const cuuint64_t dims[3] = {static_cast<cuuint64_t>(nx), static_cast<cuuint64_t>(ny),
                                 static_cast<cuuint64_t>(nz)};
-    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(nx) * es,
-                                   static_cast<cuuint64_t>(nx) * static_cast<cuuint64_t>(ny) * es};
+    const cuuint64_t strides[2] = {static_cast<cuuint64_t>(pitch) * es,
+                                   static_cast<cuuint64_t>(pitch) * static_cast<cuuint64_t>(ny) * es};
     const cuuint32_t box[3] = {static_cast<cuuint32_t>(box_w), static_cast<cuuint32_t>(box_h), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = g_encode(map,
@@ -376,7 +358,9 @@ afd_status stats_host(afd_ctx *ctx, const float *cube, int64_t n)
     return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
 }
 
-}  // namespace
+}  // namespace afd_host
+
+using namespace afd_host;
 
 extern "C" {
 

@@ -1,0 +1,53 @@
+// The library context (opaque to callers) and the host helpers shared by the
+// translation units that implement the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/afd.h"
+
+struct afd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    int stream_bps = 0;          // streaming kernel CTAs per SM (occupancy)
+    int zc_hint = 0;             // streaming kernel z-chunk override (0 = auto)
+    afd_kernel kernel = AFD_KERNEL_AUTO;
+    int *d_err = nullptr;        // device error word (bounded-wait expiries)
+    float *scratch = nullptr;    // ping-pong partner buffer
+    size_t scratch_bytes = 0;
+    float *stage = nullptr;      // device copy for afd_filter_host
+    size_t stage_bytes = 0;
+    float *lp_scratch = nullptr; // ping-pong partner of afd_filter_ex (any storage)
+    size_t lp_scratch_bytes = 0;
+    float *fb_scratch = nullptr; // float32 pair for the afd_filter_ex fallback
+    size_t fb_scratch_bytes = 0;
+    bool tb_ready[4][9] = {};    // tb_prepare done, per storage kind and depth
+    double *d_part = nullptr;    // stats partials
+    int part_blocks = 0;
+    double *d_out4 = nullptr;    // stats result (device)
+    double *h_out4 = nullptr;    // stats result (pinned host)
+    uint64_t launches = 0;
+    char errstr[256] = {0};
+};
+
+
+namespace afd_host {
+
+afd_status cuda_fail(afd_ctx *ctx, cudaError_t e);
+afd_status device_alloc(afd_ctx *ctx, void **p, size_t bytes);
+afd_status set_device(afd_ctx *ctx);
+bool dims_ok(int64_t nx, int64_t ny, int64_t nz);
+bool params_ok(const float *spacing, float K, float dt, int n_iter, afd_conductance cond);
+bool pow2_scale_ok(float scale);
+bool storage_ok(int s);
+afd_status encode_box_map(afd_ctx *ctx, CUtensorMap *map, const void *ptr, int S, int box_w,
+                          int box_h, int nx, int ny, int nz);
+// As encode_box_map, with an explicit row pitch in elements (>= nx).
+afd_status encode_pitched_map(afd_ctx *ctx, CUtensorMap *map, const void *ptr, int S, int box_w,
+                              int box_h, int nx, int ny, int nz, int64_t pitch);
+
+}  // namespace afd_host

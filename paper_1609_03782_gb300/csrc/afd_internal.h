@@ -47,6 +47,24 @@ cudaError_t launch_pm_stream_s(int S, int cond, const CUtensorMap &tmap_in, void
                                cudaStream_t stream);
 void pm_stream_box(int S, int *box_w, int *box_h, int *hx);
 
+// ---- a resident batch of cubes (streaming kernel over many cubes) ---------
+// Per-cube descriptor in device memory.  Roles: 0 input (resident), 1 result,
+// 2 scratch.  Rows are padded to `px` elements (a multiple of 16 bytes), which
+// is all the TMA needs, so any nx is streamed.
+struct BatchDesc {
+    CUtensorMap map[3];  // TMA descriptors of the three role buffers
+    void *buf[3];        // role buffers of this cube (storage format)
+    int64_t px;          // row pitch in elements
+    int nx, ny, nz;
+    int tiles_x, tiles_y, zc;
+    Coef coef;  // per-call coefficients, written on the device
+    float K;    // K of the last call, value units
+};
+
+cudaError_t launch_pm_batch(int S, int cond, const BatchDesc *desc, const int2 *list,
+                            int64_t ntiles, int src_role, int dst_role, int grid, int *err,
+                            cudaStream_t stream);
+
 // ---- temporally blocked kernel (T iterations per pass, any storage) --------
 struct TbShape {
     int tx, ty;          // interior tile

@@ -145,6 +145,24 @@ struct Packed {
     f2_t ax, ay, az, bx, by, bz, z;
 };
 
+// A quad that straddles the cube's x face (only its first m < 4 voxels are
+// inside, possible when rows are padded): the outside lanes take the last
+// inside value, so the x face at the cube boundary has delta = +0 (zero
+// flux); the outside lanes' own results are never used.
+__device__ __forceinline__ Q clamp_quad(Q c, int m)
+{
+    if (m == 1) {
+        const float c0 = f2_lo(c.a);
+        return {f2_pack(c0, c0), f2_pack(c0, c0)};
+    }
+    if (m == 2) {
+        const float c1 = f2_hi(c.a);
+        return {c.a, f2_pack(c1, c1)};
+    }
+    const float c2 = f2_lo(c.b);
+    return {c.a, f2_pack(c2, c2)};
+}
+
 // x fluxes of one row: voxel sums s_x = G_x+ - G_x- for the quad (c0..c3)
 // given its left neighbour xl and right neighbour xr.  The x faces are
 // F0 (xl|c0) F1 (c0|c1) F2 (c1|c2) F3 (c2|c3) F4 (c3|xr); F4 is passed in
@@ -162,11 +180,82 @@ __device__ __forceinline__ Q x_sums(Q c, float xl, float f4, const Packed &k)
     return {f2_sub(f12, f01), f2_sub(f34, f23)};
 }
 
-template <int S, int C>
-__global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
-    pm_step_stream(const __grid_constant__ CUtensorMap tmap, typename Store<S>::T *__restrict__ out,
-                   int nx, int ny, int nz, int tiles_x, int tiles_y, int zc, int64_t ntiles,
-                   Coef kc, int *err)
+// Where a tile's planes come from and where its result goes.
+template <int S>
+struct TileInfo {
+    int x0, y0, z0, z1, zlo, np;
+    int nx, ny, nz;
+    int64_t px;     // output row pitch (elements)
+    const void *map;  // TMA descriptor (generic address)
+    typename Store<S>::T *out;
+    Coef k;
+};
+
+__device__ __forceinline__ void chunk_planes(int tz, int zc, int nz, int &z0, int &z1, int &zlo,
+                                             int &np)
+{
+    z0 = tz * zc;
+    z1 = min(z0 + zc, nz);
+    zlo = max(z0 - 1, 0);
+    np = min(z1, nz - 1) - zlo + 1;
+}
+
+// One cube, described by kernel parameters (dense rows: pitch nx).
+template <int S>
+struct OneCube {
+    const void *map;
+    typename Store<S>::T *out;
+    int nx, ny, nz, tiles_x, tiles_y, zc;
+    Coef k;
+    __device__ __forceinline__ void tile(int64_t t, TileInfo<S> &ti) const
+    {
+        const TileCoord tc = decode_tile(t, tiles_x, tiles_y, zc, nz);
+        ti.x0 = tc.x0;
+        ti.y0 = tc.y0;
+        ti.z0 = tc.z0;
+        ti.z1 = tc.z1;
+        ti.zlo = tc.zlo;
+        ti.np = tc.np;
+        ti.nx = nx;
+        ti.ny = ny;
+        ti.nz = nz;
+        ti.px = nx;
+        ti.map = map;
+        ti.out = out;
+        ti.k = k;
+    }
+};
+
+// Many cubes of a resident batch: per-cube descriptors in global memory and a
+// list of (cube, tile) pairs; `src` and `dst` select the buffers (roles).
+template <int S>
+struct ManyCubes {
+    const BatchDesc *desc;
+    const int2 *list;
+    int src, dst;
+    __device__ __forceinline__ void tile(int64_t t, TileInfo<S> &ti) const
+    {
+        const int2 ct = list[t];
+        const BatchDesc &d = desc[ct.x];
+        const int txy = d.tiles_x * d.tiles_y;
+        const int tz = ct.y / txy;
+        const int r = ct.y - tz * txy;
+        const int ty = r / d.tiles_x;
+        ti.x0 = (r - ty * d.tiles_x) * TX;
+        ti.y0 = ty * TY;
+        chunk_planes(tz, d.zc, d.nz, ti.z0, ti.z1, ti.zlo, ti.np);
+        ti.nx = d.nx;
+        ti.ny = d.ny;
+        ti.nz = d.nz;
+        ti.px = d.px;
+        ti.map = &d.map[src];
+        ti.out = static_cast<typename Store<S>::T *>(d.buf[dst]);
+        ti.k = d.coef;
+    }
+};
+
+template <int S, int C, class Src>
+__device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int *err)
 {
     typedef Slot<S> SL;
     extern __shared__ unsigned char smem_raw[];
@@ -192,14 +281,15 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
         if (lane == 0) {
             uint32_t kk = 0;
             for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-                const TileCoord tc = decode_tile(t, tiles_x, tiles_y, zc, nz);
+                TileInfo<S> tc;
+                src.tile(t, tc);
                 for (int j = 0; j < tc.np; ++j, ++kk) {
                     const uint32_t slot = kk & (NSLOT - 1);
                     const uint32_t use = kk / NSLOT;
                     if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1u, err, kErrWaitEmpty))
                         return;
                     mbar_arrive_expect_tx(&full[slot], SL::BOX_BYTES);
-                    tma_load_3d(slots + slot * SLOT_BYTES_MAX, &tmap, tc.x0 - SL::HX, tc.y0 - 1,
+                    tma_load_3d(slots + slot * SLOT_BYTES_MAX, tc.map, tc.x0 - SL::HX, tc.y0 - 1,
                                 tc.zlo + j, &full[slot]);
                 }
             }
@@ -208,23 +298,25 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
     }
 
     // ---------------- consumers ----------------
-    Packed k;
-    k.ax = f2_pack(kc.ax, kc.ax);
-    k.ay = f2_pack(kc.ay, kc.ay);
-    k.az = f2_pack(kc.az, kc.az);
-    k.bx = f2_pack(kc.bx, kc.bx);
-    k.by = f2_pack(kc.by, kc.by);
-    k.bz = f2_pack(kc.bz, kc.bz);
-    k.z = f2_pack(kc.nz, kc.nz);
     const int qx = threadIdx.x & 15;
     const int ry = threadIdx.x >> 4;
-    const int r0 = 1 + 2 * ry;                      // slot row of the first row
+    const int r0 = 1 + 2 * ry;                       // slot row of the first row
     const int cen0 = r0 * SL::PX + SL::HX + 4 * qx;  // quad of row 0 in a slot (elements)
     const int cen1 = cen0 + SL::PX;                  // quad of row 1
     uint32_t kk = 0;
 
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const TileCoord tc = decode_tile(t, tiles_x, tiles_y, zc, nz);
+        TileInfo<S> tc;
+        src.tile(t, tc);
+        const int nx = tc.nx, ny = tc.ny, nz = tc.nz;
+        Packed k;
+        k.ax = f2_pack(tc.k.ax, tc.k.ax);
+        k.ay = f2_pack(tc.k.ay, tc.k.ay);
+        k.az = f2_pack(tc.k.az, tc.k.az);
+        k.bx = f2_pack(tc.k.bx, tc.k.bx);
+        k.by = f2_pack(tc.k.by, tc.k.by);
+        k.bz = f2_pack(tc.k.bz, tc.k.bz);
+        k.z = f2_pack(tc.k.nz, tc.k.nz);
         const int x = tc.x0 + 4 * qx;
         const int ya = tc.y0 + 2 * ry;  // row 0
         const int yb = ya + 1;          // row 1
@@ -233,8 +325,8 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
         const bool edge = (tc.x0 == 0) || (tc.x0 + TX >= nx) || (tc.y0 == 0) ||
                           (tc.y0 + TY >= ny);
         const uint32_t kbase = kk;
-        const int64_t row_stride = nx;
-        typename Store<S>::T *out0 = out + (static_cast<int64_t>(ya) * nx + x);
+        const int64_t row_stride = tc.px;
+        typename Store<S>::T *out0 = tc.out + (static_cast<int64_t>(ya) * row_stride + x);
 
 #define RING(z) (kbase + static_cast<uint32_t>((z) - tc.zlo))
 #define SLOT_PTR(r) (slots + ((r) & (NSLOT - 1)) * SLOT_BYTES_MAX)
@@ -321,8 +413,13 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
             // ---- x: F4 of both rows in one packed op, then the in-row faces
             const f2_t c3p = f2_pack(f2_hi(cur0.b), f2_hi(cur1.b));
             const f2_t f4 = face_flux2<C>(f2_sub(f2_pack(xr0, xr1), c3p), k.ax, k.bx, k.z);
-            const Q sx0 = x_sums<C>(cur0, xl0, f2_lo(f4), k);
-            const Q sx1 = x_sums<C>(cur1, xl1, f2_hi(f4), k);
+            Q cx0 = cur0, cx1 = cur1;
+            if (edge && x < nx && x + 4 > nx) {
+                cx0 = clamp_quad(cur0, nx - x);
+                cx1 = clamp_quad(cur1, nx - x);
+            }
+            const Q sx0 = x_sums<C>(cx0, xl0, f2_lo(f4), k);
+            const Q sx1 = x_sums<C>(cx1, xl1, f2_hi(f4), k);
 
             // ---- update: I' = I + ((s_x + s_y) + s_z)
             const Q o0 = {pm_update2(cur0.a, sx0.a, f2_sub(fmid.a, fdn.a), f2_sub(fa0.a, fb0.a)),
@@ -351,6 +448,26 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
     }
 }
 
+
+template <int S, int C>
+__global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
+    pm_step_stream(const __grid_constant__ CUtensorMap tmap, typename Store<S>::T *__restrict__ out,
+                   int nx, int ny, int nz, int tiles_x, int tiles_y, int zc, int64_t ntiles,
+                   Coef kc, int *err)
+{
+    const OneCube<S> src{&tmap, out, nx, ny, nz, tiles_x, tiles_y, zc, kc};
+    stream_body<S, C>(src, ntiles, err);
+}
+
+template <int S, int C>
+__global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
+    pm_step_batch(const BatchDesc *__restrict__ desc, const int2 *__restrict__ list,
+                  int64_t ntiles, int src_role, int dst_role, int *err)
+{
+    const ManyCubes<S> src{desc, list, src_role, dst_role};
+    stream_body<S, C>(src, ntiles, err);
+}
+
 }  // namespace
 
 size_t pm_stream_smem_bytes()
@@ -373,6 +490,12 @@ cudaError_t stream_attr()
     return cudaFuncSetAttribute(pm_step_stream<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 static_cast<int>(pm_stream_smem_bytes()));
 }
+template <int S, int C>
+cudaError_t batch_attr()
+{
+    return cudaFuncSetAttribute(pm_step_batch<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(pm_stream_smem_bytes()));
+}
 template <int S>
 cudaError_t stream_attr_all()
 {
@@ -381,6 +504,12 @@ cudaError_t stream_attr_all()
         e = stream_attr<S, COND_RAT>();
     if (e == cudaSuccess)
         e = stream_attr<S, COND_LIN>();
+    if (e == cudaSuccess)
+        e = batch_attr<S, COND_EXP>();
+    if (e == cudaSuccess)
+        e = batch_attr<S, COND_RAT>();
+    if (e == cudaSuccess)
+        e = batch_attr<S, COND_LIN>();
     return e;
 }
 }  // namespace
@@ -487,6 +616,50 @@ cudaError_t launch_pm_stream_s(int S, int cond, const CUtensorMap &tmap_in, void
         return stream_launch_c<STORE_BF16>(cond, tmap_in, out, nx, ny, nz, k, plan, err, stream);
     default:
         return stream_launch_c<STORE_I16>(cond, tmap_in, out, nx, ny, nz, k, plan, err, stream);
+    }
+}
+
+namespace {
+template <int S>
+cudaError_t batch_launch_c(int cond, const BatchDesc *desc, const int2 *list, int64_t ntiles,
+                           int src, int dst, int grid, int *err, cudaStream_t stream)
+{
+    const size_t smem = pm_stream_smem_bytes();
+    switch (cond) {
+    case COND_EXP:
+        pm_step_batch<S, COND_EXP><<<grid, kStreamThreads, smem, stream>>>(desc, list, ntiles, src,
+                                                                          dst, err);
+        break;
+    case COND_RAT:
+        pm_step_batch<S, COND_RAT><<<grid, kStreamThreads, smem, stream>>>(desc, list, ntiles, src,
+                                                                          dst, err);
+        break;
+    default:
+        pm_step_batch<S, COND_LIN><<<grid, kStreamThreads, smem, stream>>>(desc, list, ntiles, src,
+                                                                          dst, err);
+        break;
+    }
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_pm_batch(int S, int cond, const BatchDesc *desc, const int2 *list,
+                            int64_t ntiles, int src_role, int dst_role, int grid, int *err,
+                            cudaStream_t stream)
+{
+    switch (S) {
+    case STORE_F32:
+        return batch_launch_c<STORE_F32>(cond, desc, list, ntiles, src_role, dst_role, grid, err,
+                                         stream);
+    case STORE_F16:
+        return batch_launch_c<STORE_F16>(cond, desc, list, ntiles, src_role, dst_role, grid, err,
+                                         stream);
+    case STORE_BF16:
+        return batch_launch_c<STORE_BF16>(cond, desc, list, ntiles, src_role, dst_role, grid, err,
+                                          stream);
+    default:
+        return batch_launch_c<STORE_I16>(cond, desc, list, ntiles, src_role, dst_role, grid, err,
+                                         stream);
     }
 }
 
