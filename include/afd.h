@@ -42,6 +42,7 @@
 #ifndef AFD_H
 #define AFD_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -284,6 +285,57 @@ afd_status afd_batch_set_zchunk(afd_batch *b, int zc);
 /* Free the batch's device memory after the context's stream is idle.  NULL
  * is accepted. */
 afd_status afd_batch_destroy(afd_batch *b);
+
+/* ---- interactive re-filter service (continuous batching) ----
+ *
+ * A service runs re-filter requests (cube of a resident batch, K, dt,
+ * n_iter, conductance) against the batch's resident inputs.  Requests are
+ * admitted while a descriptor slot and slot memory for their result and
+ * scratch cubes fit the service's HBM budget; each round is one launch of
+ * the batched streaming kernel per conductance kind over the tiles of every
+ * admitted request, each advancing one iteration.  Requests submitted while
+ * others run join at the next round.  A request's result is bit-identical
+ * to afd_filter_ex (t_block 1) on that cube alone.  The paper's aim is
+ * interactive filtering of faint structure (Sec. 1, Sec. 6). */
+typedef struct afd_serve afd_serve;
+
+/* mem_bytes: HBM budget for request results and scratch (allocated once).
+ * max_active: most requests admitted at once.  The batch must belong to
+ * ctx and outlive the service. */
+afd_status afd_serve_create(afd_ctx *ctx, afd_batch *cubes, size_t mem_bytes, int max_active,
+                            afd_serve **out);
+
+/* Queue a request; *ticket identifies it.  K in value units (> 0; +inf is
+ * the heat equation), dt and cond as for afd_filter, unit spacing.
+ * AFD_ENOMEM if the request could never fit the budget.  Host-side only. */
+afd_status afd_serve_submit(afd_serve *s, int cube, float K, float dt, int n_iter,
+                            afd_conductance cond, uint64_t *ticket);
+
+/* Advance the service: retire finished rounds, admit queued requests that
+ * fit, launch the next round if fewer than two are in flight.  wait != 0
+ * blocks for the oldest round when nothing new could be launched.  *active
+ * and *queued (may be NULL) receive the counts afterwards. */
+afd_status afd_serve_step(afd_serve *s, int wait, int *active, int *queued);
+
+/* *state: 0 queued, 1 running, 2 done; *latency_s (may be NULL): seconds
+ * from submit to the completion of its last round as seen by a step (-1 if
+ * not done).  AFD_EINVAL for an unknown ticket. */
+afd_status afd_serve_poll(afd_serve *s, uint64_t ticket, int *state, double *latency_s);
+
+/* Copy a done request's result (dense, the batch's storage format) to a
+ * DEVICE or HOST pointer; asynchronous on the context's stream.  AFD_EBUSY
+ * if not done. */
+afd_status afd_serve_result(afd_serve *s, uint64_t ticket, void *dst);
+
+/* Free a done request's slot memory (after its result has been copied).
+ * AFD_EBUSY if not done. */
+afd_status afd_serve_release(afd_serve *s, uint64_t ticket);
+
+/* Bytes of the budget not held by admitted requests. */
+afd_status afd_serve_free_bytes(afd_serve *s, size_t *out);
+
+/* Free the service after the context's stream is idle.  NULL is accepted. */
+afd_status afd_serve_destroy(afd_serve *s);
 
 /* Largest cube afd_filter_noalloc accepts: 8,388,608 voxels, i.e. 32 MiB of
  * float32 scratch (for example 256 x 256 x 128). */

@@ -60,6 +60,16 @@ def _load():
         "afd_batch_k": ([vp, vp], c_int),
         "afd_batch_set_zchunk": ([vp, c_int], c_int),
         "afd_batch_destroy": ([vp], c_int),
+        "afd_serve_create": ([vp, vp, ctypes.c_size_t, c_int, ctypes.POINTER(vp)], c_int),
+        "afd_serve_submit": ([vp, c_int, f32, f32, c_int, c_int,
+                              ctypes.POINTER(ctypes.c_uint64)], c_int),
+        "afd_serve_step": ([vp, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)], c_int),
+        "afd_serve_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(c_int),
+                            ctypes.POINTER(ctypes.c_double)], c_int),
+        "afd_serve_result": ([vp, ctypes.c_uint64, vp], c_int),
+        "afd_serve_release": ([vp, ctypes.c_uint64], c_int),
+        "afd_serve_free_bytes": ([vp, ctypes.POINTER(ctypes.c_size_t)], c_int),
+        "afd_serve_destroy": ([vp], c_int),
         "afd_filter_noalloc": ([vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int, vp], c_int),
         "afd_stats": ([vp, vp, i64, vp], c_int),
         "afd_noise_rms": ([vp, vp, i64, dp], c_int),
@@ -349,6 +359,83 @@ def afd_batch_set_zchunk(b: Batch, zc: int) -> None:
 
 def afd_batch_destroy(b: Batch) -> None:
     b.close()
+
+
+class Server:
+    """An interactive re-filter service over a resident Batch (afd_serve*)."""
+
+    def __init__(self, batch: Batch, mem_bytes: int, max_active: int = 64):
+        self.batch = batch
+        h = ctypes.c_void_p()
+        _check(_lib.afd_serve_create(batch.ctx.handle, batch.handle, int(mem_bytes),
+                                     int(max_active), ctypes.byref(h)), "afd_serve_create",
+               batch.ctx)
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            _lib.afd_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def afd_serve_create(batch: Batch, mem_bytes: int, max_active: int = 64) -> Server:
+    return Server(batch, mem_bytes, max_active)
+
+
+def afd_serve_submit(srv: Server, cube: int, K: float, dt: float, n_iter: int,
+                     conductance: str = "rational") -> int:
+    t = ctypes.c_uint64()
+    _check(_lib.afd_serve_submit(srv.handle, int(cube), float(K), float(dt), int(n_iter),
+                                 COND[conductance], ctypes.byref(t)), "afd_serve_submit",
+           srv.batch.ctx)
+    return t.value
+
+
+def afd_serve_step(srv: Server, wait: bool = False):
+    """Advance the service; returns (active, queued)."""
+    a, q = ctypes.c_int(), ctypes.c_int()
+    _use_current_stream(srv.batch.ctx)
+    _check(_lib.afd_serve_step(srv.handle, int(bool(wait)), ctypes.byref(a), ctypes.byref(q)),
+           "afd_serve_step", srv.batch.ctx)
+    return a.value, q.value
+
+
+def afd_serve_poll(srv: Server, ticket: int):
+    """(state, latency seconds): state 0 queued, 1 running, 2 done."""
+    st, lat = ctypes.c_int(), ctypes.c_double()
+    _check(_lib.afd_serve_poll(srv.handle, int(ticket), ctypes.byref(st), ctypes.byref(lat)),
+           "afd_serve_poll", srv.batch.ctx)
+    return st.value, lat.value
+
+
+def afd_serve_result(srv: Server, ticket: int, out: torch.Tensor) -> torch.Tensor:
+    if not out.is_contiguous():
+        raise ValueError("out must be contiguous")
+    _use_current_stream(srv.batch.ctx, out if out.is_cuda else None)
+    _check(_lib.afd_serve_result(srv.handle, int(ticket), ctypes.c_void_p(out.data_ptr())),
+           "afd_serve_result", srv.batch.ctx)
+    return out
+
+
+def afd_serve_release(srv: Server, ticket: int) -> None:
+    _check(_lib.afd_serve_release(srv.handle, int(ticket)), "afd_serve_release", srv.batch.ctx)
+
+
+def afd_serve_free_bytes(srv: Server) -> int:
+    out = ctypes.c_size_t()
+    _check(_lib.afd_serve_free_bytes(srv.handle, ctypes.byref(out)), "afd_serve_free_bytes",
+           srv.batch.ctx)
+    return out.value
+
+
+def afd_serve_destroy(srv: Server) -> None:
+    srv.close()
 
 
 NOALLOC_MAX_VOXELS = 8388608

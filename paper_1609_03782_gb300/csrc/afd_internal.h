@@ -61,9 +61,11 @@ struct BatchDesc {
     float K;    // K of the last call, value units
 };
 
+// roles: null (all descriptors use src_role/dst_role) or per-descriptor
+// (src, dst) pairs in device memory.
 cudaError_t launch_pm_batch(int S, int cond, const BatchDesc *desc, const int2 *list,
-                            int64_t ntiles, int src_role, int dst_role, int grid, int *err,
-                            cudaStream_t stream);
+                            const int2 *roles, int64_t ntiles, int src_role, int dst_role, int grid,
+                            int *err, cudaStream_t stream);
 
 // ---- temporally blocked kernel (T iterations per pass, any storage) --------
 struct TbShape {

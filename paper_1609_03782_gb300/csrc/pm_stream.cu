@@ -227,11 +227,13 @@ struct OneCube {
 };
 
 // Many cubes of a resident batch: per-cube descriptors in global memory and a
-// list of (cube, tile) pairs; `src` and `dst` select the buffers (roles).
+// list of (cube, tile) pairs; `src` and `dst` select the buffers (roles), or
+// per descriptor `roles[c]` = (src, dst) when roles is not null.
 template <int S>
 struct ManyCubes {
     const BatchDesc *desc;
     const int2 *list;
+    const int2 *roles;
     int src, dst;
     __device__ __forceinline__ void tile(int64_t t, TileInfo<S> &ti) const
     {
@@ -248,8 +250,14 @@ struct ManyCubes {
         ti.ny = d.ny;
         ti.nz = d.nz;
         ti.px = d.px;
-        ti.map = &d.map[src];
-        ti.out = static_cast<typename Store<S>::T *>(d.buf[dst]);
+        int sr = src, dr = dst;
+        if (roles) {
+            const int2 rr = roles[ct.x];
+            sr = rr.x;
+            dr = rr.y;
+        }
+        ti.map = &d.map[sr];
+        ti.out = static_cast<typename Store<S>::T *>(d.buf[dr]);
         ti.k = d.coef;
     }
 };
@@ -462,9 +470,10 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
 template <int S, int C>
 __global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
     pm_step_batch(const BatchDesc *__restrict__ desc, const int2 *__restrict__ list,
-                  int64_t ntiles, int src_role, int dst_role, int *err)
+                  const int2 *__restrict__ roles, int64_t ntiles, int src_role, int dst_role,
+                  int *err)
 {
-    const ManyCubes<S> src{desc, list, src_role, dst_role};
+    const ManyCubes<S> src{desc, list, roles, src_role, dst_role};
     stream_body<S, C>(src, ntiles, err);
 }
 
@@ -621,22 +630,23 @@ cudaError_t launch_pm_stream_s(int S, int cond, const CUtensorMap &tmap_in, void
 
 namespace {
 template <int S>
-cudaError_t batch_launch_c(int cond, const BatchDesc *desc, const int2 *list, int64_t ntiles,
-                           int src, int dst, int grid, int *err, cudaStream_t stream)
+cudaError_t batch_launch_c(int cond, const BatchDesc *desc, const int2 *list, const int2 *roles,
+                           int64_t ntiles, int src, int dst, int grid, int *err,
+                           cudaStream_t stream)
 {
     const size_t smem = pm_stream_smem_bytes();
     switch (cond) {
     case COND_EXP:
-        pm_step_batch<S, COND_EXP><<<grid, kStreamThreads, smem, stream>>>(desc, list, ntiles, src,
-                                                                          dst, err);
+        pm_step_batch<S, COND_EXP><<<grid, kStreamThreads, smem, stream>>>(desc, list, roles, ntiles,
+                                                                          src, dst, err);
         break;
     case COND_RAT:
-        pm_step_batch<S, COND_RAT><<<grid, kStreamThreads, smem, stream>>>(desc, list, ntiles, src,
-                                                                          dst, err);
+        pm_step_batch<S, COND_RAT><<<grid, kStreamThreads, smem, stream>>>(desc, list, roles, ntiles,
+                                                                          src, dst, err);
         break;
     default:
-        pm_step_batch<S, COND_LIN><<<grid, kStreamThreads, smem, stream>>>(desc, list, ntiles, src,
-                                                                          dst, err);
+        pm_step_batch<S, COND_LIN><<<grid, kStreamThreads, smem, stream>>>(desc, list, roles, ntiles,
+                                                                          src, dst, err);
         break;
     }
     return cudaGetLastError();
@@ -644,21 +654,21 @@ cudaError_t batch_launch_c(int cond, const BatchDesc *desc, const int2 *list, in
 }  // namespace
 
 cudaError_t launch_pm_batch(int S, int cond, const BatchDesc *desc, const int2 *list,
-                            int64_t ntiles, int src_role, int dst_role, int grid, int *err,
-                            cudaStream_t stream)
+                            const int2 *roles, int64_t ntiles, int src_role, int dst_role, int grid,
+                            int *err, cudaStream_t stream)
 {
     switch (S) {
     case STORE_F32:
-        return batch_launch_c<STORE_F32>(cond, desc, list, ntiles, src_role, dst_role, grid, err,
+        return batch_launch_c<STORE_F32>(cond, desc, list, roles, ntiles, src_role, dst_role, grid, err,
                                          stream);
     case STORE_F16:
-        return batch_launch_c<STORE_F16>(cond, desc, list, ntiles, src_role, dst_role, grid, err,
+        return batch_launch_c<STORE_F16>(cond, desc, list, roles, ntiles, src_role, dst_role, grid, err,
                                          stream);
     case STORE_BF16:
-        return batch_launch_c<STORE_BF16>(cond, desc, list, ntiles, src_role, dst_role, grid, err,
+        return batch_launch_c<STORE_BF16>(cond, desc, list, roles, ntiles, src_role, dst_role, grid, err,
                                           stream);
     default:
-        return batch_launch_c<STORE_I16>(cond, desc, list, ntiles, src_role, dst_role, grid, err,
+        return batch_launch_c<STORE_I16>(cond, desc, list, roles, ntiles, src_role, dst_role, grid, err,
                                          stream);
     }
 }
