@@ -262,6 +262,105 @@ struct ManyCubes {
     }
 };
 
+// Everything one consumer thread needs for its 4 x 2 block of a tile.
+template <int S>
+struct PlaneArgs {
+    const unsigned char *slots;
+    uint64_t *full, *empty;
+    int *err;
+    uint32_t kbase;
+    int zlo, nx, ny, nz, cen0, cen1, x, ya, yb, lane;
+    bool edge, act0, act1;
+    typename Store<S>::T *out0;
+    int64_t row_stride;
+};
+
+// One plane z of the block: reads the plane above (waiting for its TMA),
+// computes and stores the block's 8 results, releases plane z's slot.
+// In: the current plane (cur) and the flux through its lower z face (fb).
+// Out: the plane above (n) and the flux through the upper face (fa), the next
+// plane's cur and fb.  Returns false if a bounded wait expired.
+template <int S, int C>
+__device__ __forceinline__ bool plane_step(const PlaneArgs<S> &a, const Packed &k, int z,
+                                           const Q &cur0, const Q &cur1, const Q &fb0,
+                                           const Q &fb1, Q &n0, Q &n1, Q &fa0, Q &fa1)
+{
+    typedef Slot<S> SL;
+    const uint32_t rc = a.kbase + static_cast<uint32_t>(z - a.zlo);
+    const unsigned char *s = a.slots + (rc & (NSLOT - 1)) * SLOT_BYTES_MAX;
+    // ---- z: the plane above and the flux through the upper face
+    if (z + 1 < a.nz) {
+        const uint32_t rn = rc + 1;
+        if (!mbar_wait(&a.full[rn & (NSLOT - 1)], (rn / NSLOT) & 1u, a.err, kErrWaitFull))
+            return false;
+        const unsigned char *sn = a.slots + (rn & (NSLOT - 1)) * SLOT_BYTES_MAX;
+        n0 = lds_qs<S>(sn, a.cen0);
+        n1 = lds_qs<S>(sn, a.cen1);
+    } else {
+        n0 = cur0;  // zero flux at z = nz-1
+        n1 = cur1;
+    }
+    fa0 = q_flux<C>(q_sub(n0, cur0), k.az, k.bz, k.z);
+    fa1 = q_flux<C>(q_sub(n1, cur1), k.az, k.bz, k.z);
+
+    // ---- neighbours in the plane (own value across a cube face)
+    Q dn = lds_qs<S>(s, a.cen0 - SL::PX);
+    Q up = lds_qs<S>(s, a.cen1 + SL::PX);
+    Q mid = cur1;
+    float xl0 = lds_s<S>(s, a.cen0 - 1), xr0 = lds_s<S>(s, a.cen0 + 4);
+    float xl1 = lds_s<S>(s, a.cen1 - 1), xr1 = lds_s<S>(s, a.cen1 + 4);
+    Q cx0 = cur0, cx1 = cur1;
+    if (a.edge) {
+        const float c0a = f2_lo(cur0.a), c3a = f2_hi(cur0.b);
+        const float c0b = f2_lo(cur1.a), c3b = f2_hi(cur1.b);
+        if (a.ya == 0)
+            dn = cur0;
+        if (a.yb >= a.ny)
+            mid = cur0;
+        if (a.yb + 1 >= a.ny)
+            up = cur1;
+        if (a.x == 0) {
+            xl0 = c0a;
+            xl1 = c0b;
+        }
+        if (a.x + 4 >= a.nx) {
+            xr0 = c3a;
+            xr1 = c3b;
+        }
+        if (a.x < a.nx && a.x + 4 > a.nx) {
+            cx0 = clamp_quad(cur0, a.nx - a.x);
+            cx1 = clamp_quad(cur1, a.nx - a.x);
+        }
+    }
+
+    // ---- y: faces (dn|row0), (row0|row1), (row1|up)
+    const Q fdn = q_flux<C>(q_sub(cur0, dn), k.ay, k.by, k.z);
+    const Q fmid = q_flux<C>(q_sub(mid, cur0), k.ay, k.by, k.z);
+    const Q fup = q_flux<C>(q_sub(up, cur1), k.ay, k.by, k.z);
+
+    // ---- x: F4 of both rows in one packed op, then the in-row faces
+    const f2_t c3p = f2_pack(f2_hi(cur0.b), f2_hi(cur1.b));
+    const f2_t f4 = face_flux2<C>(f2_sub(f2_pack(xr0, xr1), c3p), k.ax, k.bx, k.z);
+    const Q sx0 = x_sums<C>(cx0, xl0, f2_lo(f4), k);
+    const Q sx1 = x_sums<C>(cx1, xl1, f2_hi(f4), k);
+
+    // ---- update: I' = I + ((s_x + s_y) + s_z)
+    const Q o0 = {pm_update2(cur0.a, sx0.a, f2_sub(fmid.a, fdn.a), f2_sub(fa0.a, fb0.a)),
+                  pm_update2(cur0.b, sx0.b, f2_sub(fmid.b, fdn.b), f2_sub(fa0.b, fb0.b))};
+    const Q o1 = {pm_update2(cur1.a, sx1.a, f2_sub(fup.a, fmid.a), f2_sub(fa1.a, fb1.a)),
+                  pm_update2(cur1.b, sx1.b, f2_sub(fup.b, fmid.b), f2_sub(fa1.b, fb1.b))};
+    typename Store<S>::T *po = a.out0 + static_cast<int64_t>(z) * a.ny * a.row_stride;
+    if (a.act0)
+        stg_q<S>(po, o0);
+    if (a.act1)
+        stg_q<S>(po + a.row_stride, o1);
+
+    __syncwarp();
+    if (a.lane == 0)
+        mbar_arrive(&a.empty[rc & (NSLOT - 1)]);
+    return true;
+}
+
 template <int S, int C, class Src>
 __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int *err)
 {
@@ -371,80 +470,20 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
             }
         }
 
-        for (int z = tc.z0; z < tc.z1; ++z) {
-            const uint32_t rc = RING(z);
-            const unsigned char *s = SLOT_PTR(rc);
-            // ---- z: the plane above and the flux through the upper face
-            Q n0, n1, fa0, fa1;
-            if (z + 1 < nz) {
-                const uint32_t rn = RING(z + 1);
-                WAIT_FULL(rn);
-                n0 = lds_qs<S>(SLOT_PTR(rn), cen0);
-                n1 = lds_qs<S>(SLOT_PTR(rn), cen1);
-            } else {
-                n0 = cur0;  // zero flux at z = nz-1
-                n1 = cur1;
-            }
-            fa0 = q_flux<C>(q_sub(n0, cur0), k.az, k.bz, k.z);
-            fa1 = q_flux<C>(q_sub(n1, cur1), k.az, k.bz, k.z);
-
-            // ---- neighbours in the plane (own value across a cube face)
-            Q dn = lds_qs<S>(s, cen0 - SL::PX);
-            Q up = lds_qs<S>(s, cen1 + SL::PX);
-            Q mid = cur1;
-            float xl0 = lds_s<S>(s, cen0 - 1), xr0 = lds_s<S>(s, cen0 + 4);
-            float xl1 = lds_s<S>(s, cen1 - 1), xr1 = lds_s<S>(s, cen1 + 4);
-            if (edge) {
-                float c0a = f2_lo(cur0.a), c3a = f2_hi(cur0.b);
-                float c0b = f2_lo(cur1.a), c3b = f2_hi(cur1.b);
-                if (ya == 0)
-                    dn = cur0;
-                if (yb >= ny)
-                    mid = cur0;
-                if (yb + 1 >= ny)
-                    up = cur1;
-                if (x == 0) {
-                    xl0 = c0a;
-                    xl1 = c0b;
-                }
-                if (x + 4 >= nx) {
-                    xr0 = c3a;
-                    xr1 = c3b;
-                }
-            }
-
-            // ---- y: faces (dn|row0), (row0|row1), (row1|up)
-            const Q fdn = q_flux<C>(q_sub(cur0, dn), k.ay, k.by, k.z);
-            const Q fmid = q_flux<C>(q_sub(mid, cur0), k.ay, k.by, k.z);
-            const Q fup = q_flux<C>(q_sub(up, cur1), k.ay, k.by, k.z);
-
-            // ---- x: F4 of both rows in one packed op, then the in-row faces
-            const f2_t c3p = f2_pack(f2_hi(cur0.b), f2_hi(cur1.b));
-            const f2_t f4 = face_flux2<C>(f2_sub(f2_pack(xr0, xr1), c3p), k.ax, k.bx, k.z);
-            Q cx0 = cur0, cx1 = cur1;
-            if (edge && x < nx && x + 4 > nx) {
-                cx0 = clamp_quad(cur0, nx - x);
-                cx1 = clamp_quad(cur1, nx - x);
-            }
-            const Q sx0 = x_sums<C>(cx0, xl0, f2_lo(f4), k);
-            const Q sx1 = x_sums<C>(cx1, xl1, f2_hi(f4), k);
-
-            // ---- update: I' = I + ((s_x + s_y) + s_z)
-            const Q o0 = {pm_update2(cur0.a, sx0.a, f2_sub(fmid.a, fdn.a), f2_sub(fa0.a, fb0.a)),
-                          pm_update2(cur0.b, sx0.b, f2_sub(fmid.b, fdn.b), f2_sub(fa0.b, fb0.b))};
-            const Q o1 = {pm_update2(cur1.a, sx1.a, f2_sub(fup.a, fmid.a), f2_sub(fa1.a, fb1.a)),
-                          pm_update2(cur1.b, sx1.b, f2_sub(fup.b, fmid.b), f2_sub(fa1.b, fb1.b))};
-            typename Store<S>::T *po = out0 + static_cast<int64_t>(z) * ny * row_stride;
-            if (act0)
-                stg_q<S>(po, o0);
-            if (act1)
-                stg_q<S>(po + row_stride, o1);
-
-            RELEASE(rc);
-            cur0 = n0;
-            cur1 = n1;
-            fb0 = fa0;
-            fb1 = fa1;
+        const PlaneArgs<S> pa{slots, full, empty, err, kbase, tc.zlo, nx, ny, nz, cen0, cen1,
+                              x, ya, yb, lane, edge, act0, act1, out0, row_stride};
+        // two planes per iteration with the register roles swapped: no copies
+        Q n0, n1, fa0, fa1;
+        int z = tc.z0;
+        for (; z + 1 < tc.z1; z += 2) {
+            if (!plane_step<S, C>(pa, k, z, cur0, cur1, fb0, fb1, n0, n1, fa0, fa1))
+                return;
+            if (!plane_step<S, C>(pa, k, z + 1, n0, n1, fa0, fa1, cur0, cur1, fb0, fb1))
+                return;
+        }
+        if (z < tc.z1) {
+            if (!plane_step<S, C>(pa, k, z, cur0, cur1, fb0, fb1, n0, n1, fa0, fa1))
+                return;
         }
         if (tc.z1 < nz)
             RELEASE(RING(tc.z1));  // the halo plane above the chunk
