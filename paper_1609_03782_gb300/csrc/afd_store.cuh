@@ -55,18 +55,44 @@ struct Store<STORE_BF16> {
     }
 };
 
+// int16 <-> float32 without the conversion unit (which the conductances'
+// MUFU operations also use): the float 1.5 * 2^23 has an ulp of 1, so
+//   load:  bits(1.5*2^23) + q, reinterpreted, minus 1.5*2^23 is exactly q;
+//   store: v is first clamped to +-32767 (the same result as rounding then
+//          clamping), then v + 1.5*2^23 rounds it to an integer (to nearest,
+//          ties to even) and its bits minus bits(1.5*2^23) are that integer.
 template <>
 struct Store<STORE_I16> {
     typedef short T;
     static constexpr int bytes = 2;
-    __device__ __forceinline__ static float load(T v) { return static_cast<float>(v); }
+    __device__ __forceinline__ static float load(T v)
+    {
+        return __fsub_rn(__int_as_float(0x4B400000 + static_cast<int>(v)), 12582912.0f);
+    }
     __device__ __forceinline__ static T store(float v)
     {
-        int q = __float2int_rn(v);
-        q = max(-kI16Max, min(kI16Max, q));
-        return static_cast<short>(q);
+        const float c = fminf(fmaxf(v, -32767.0f), 32767.0f);
+        return static_cast<short>(__float_as_int(__fadd_rn(c, 12582912.0f)) - 0x4B400000);
     }
 };
+
+// Two floats -> two storage elements packed in 32 bits (low = first).  The
+// 2-byte float formats use the packed conversions (each lane rounds like the
+// scalar one).
+template <int S>
+__device__ __forceinline__ unsigned store2(float lo, float hi)
+{
+    if constexpr (S == STORE_F16) {
+        const __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const unsigned *>(&h);
+    } else if constexpr (S == STORE_BF16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const unsigned *>(&h);
+    } else {
+        return static_cast<unsigned>(static_cast<unsigned short>(Store<S>::store(lo))) |
+               (static_cast<unsigned>(static_cast<unsigned short>(Store<S>::store(hi))) << 16);
+    }
+}
 
 // Size in bytes of one element of storage kind s.
 inline int store_bytes(int s) { return s == STORE_F32 ? 4 : 2; }

@@ -133,11 +133,7 @@ __device__ __forceinline__ void stg_q(typename Store<S>::T *p, Q v)
     if constexpr (S == STORE_F32) {
         *reinterpret_cast<float4 *>(p) = o;
     } else {
-        const unsigned u0 = static_cast<unsigned short>(Store<S>::store(o.x));
-        const unsigned u1 = static_cast<unsigned short>(Store<S>::store(o.y));
-        const unsigned u2 = static_cast<unsigned short>(Store<S>::store(o.z));
-        const unsigned u3 = static_cast<unsigned short>(Store<S>::store(o.w));
-        *reinterpret_cast<uint2 *>(p) = make_uint2(u0 | (u1 << 16), u2 | (u3 << 16));
+        *reinterpret_cast<uint2 *>(p) = make_uint2(store2<S>(o.x, o.y), store2<S>(o.z, o.w));
     }
 }
 

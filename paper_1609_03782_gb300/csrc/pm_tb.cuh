@@ -135,13 +135,7 @@ __device__ __forceinline__ void store_block(typename Store<S>::T *p, Q v)
     if constexpr (S == STORE_F32) {
         *reinterpret_cast<float4 *>(p) = make_float4(f0, f1, f2, f3);
     } else {
-        typedef typename Store<S>::T E;
-        const unsigned u0 = static_cast<unsigned short>(Store<S>::store(f0));
-        const unsigned u1 = static_cast<unsigned short>(Store<S>::store(f1));
-        const unsigned u2 = static_cast<unsigned short>(Store<S>::store(f2));
-        const unsigned u3 = static_cast<unsigned short>(Store<S>::store(f3));
-        (void)sizeof(E);
-        *reinterpret_cast<uint2 *>(p) = make_uint2(u0 | (u1 << 16), u2 | (u3 << 16));
+        *reinterpret_cast<uint2 *>(p) = make_uint2(store2<S>(f0, f1), store2<S>(f2, f3));
     }
 }
 
