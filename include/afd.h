@@ -138,6 +138,26 @@ afd_status afd_filter_out(afd_ctx *ctx, const float *in, float *out, int64_t nx,
                           int64_t nz, const float *spacing, float K, float dt, int n_iter,
                           afd_conductance cond);
 
+/* The paper's own intensity-driven gradient filter (Sec. 3.3, the explicit
+ * update after eq. "conductivepara"), out of place:
+ *     I' = I + tau (C_x D_x + C_y D_y + C_z D_z) / (1 + I^2 / (K^2 rms^2))
+ * with D_a = [I(a+1) - I] + [I(a-1) - I] the nearest-neighbour second
+ * difference (a neighbour outside the cube adds nothing) and the conductance
+ * taken once per voxel from its own intensity.  It does not conserve the
+ * voxel sum (the paper notes the flux scale is not kept).
+ *   in, out  DEVICE pointers to nx*ny*nz floats (in == out allowed).
+ *   C        HOST pointer to (C_x, C_y, C_z), each >= 0 (paper range [0, 10]).
+ *   K        >= 0, in units of rms (paper range [0.5, 10], default 1.5);
+ *            K = 0 or rms = 0 is the identity, K * rms = +inf gives S = 1.
+ *   rms      the cube's noise level (e.g. afd_noise_rms).
+ *   tau      > 0 (paper range [0.0025, 0.0625], default 0.0325).
+ *   n_iter   >= 0 (paper default 20).
+ * Stable (no new extrema) for tau * 2 (C_x + C_y + C_z) <= 1.  Uses the
+ * kernels of afd_filter; asynchronous. */
+afd_status afd_filter_intensity(afd_ctx *ctx, const float *in, float *out, int64_t nx,
+                                int64_t ny, int64_t nz, const float *C, float K, float rms,
+                                float tau, int n_iter);
+
 /* afd_filter with the cube in pageable or pinned HOST memory: copies host_in
  * to context-owned device memory, filters, and copies the result to
  * host_out (host_in == host_out is allowed).  Synchronous: returns after the

@@ -48,6 +48,7 @@ def _load():
         "afd_filter": ([vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_out": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_host": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
+        "afd_filter_intensity": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, f32, c_int], c_int),
         "afd_selftest_wait": ([vp, i64], c_int),
         "afd_quantize": ([vp, vp, vp, i64, c_int, f32], c_int),
         "afd_dequantize": ([vp, vp, vp, i64, c_int, f32], c_int),
@@ -195,6 +196,25 @@ def afd_filter_out(ctx: Context, cube_in: torch.Tensor, cube_out: torch.Tensor, 
     _check(_lib.afd_filter_out(ctx.handle, p_in, p_out, nx, ny, nz, _spacing(spacing),
                                float(K), float(dt), int(n_iter), COND[conductance]),
            "afd_filter_out", ctx)
+    return cube_out
+
+
+def afd_filter_intensity(ctx: Context, cube_in: torch.Tensor, cube_out: torch.Tensor,
+                         K: float, rms: float, tau: float, n_iter: int,
+                         C=(5.0, 5.0, 5.0)) -> torch.Tensor:
+    """The paper's intensity-driven filter (K in units of rms), out of place."""
+    for t in (cube_in, cube_out):
+        if t.dtype != torch.float32 or not t.is_cuda:
+            raise ValueError("afd_filter_intensity takes float32 CUDA tensors")
+    if cube_in.shape != cube_out.shape:
+        raise ValueError("input and output shapes differ")
+    p_in, nx, ny, nz = _cube_args(cube_in)
+    p_out, _, _, _ = _cube_args(cube_out)
+    _use_current_stream(ctx, cube_in)
+    c = (ctypes.c_float * 3)(*[float(v) for v in C])
+    _check(_lib.afd_filter_intensity(ctx.handle, p_in, p_out, nx, ny, nz, c, float(K),
+                                     float(rms), float(tau), int(n_iter)),
+           "afd_filter_intensity", ctx)
     return cube_out
 
 

@@ -169,22 +169,34 @@ afd_status set_device(afd_ctx *ctx)
 // src_i = dst_{i-1}.  Out of place (in != out) the destinations alternate
 // between `out` and scratch so that the last pass lands in `out`; in place
 // they alternate starting with scratch, and an odd count ends with a copy.
+afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
+                      int64_t nz, int kind, const afd::Coef &k, int n_iter);
+
 afd_status filter_device(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
                          int64_t nz, const float *spacing, float K, float dt, int n_iter,
                          afd_conductance cond)
 {
     const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
-    cudaError_t e = cudaSuccess;
     if (n_iter == 0 || K == 0.0f) {  // identity
+        cudaError_t e = cudaSuccess;
         if (in != out)
             e = cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
         return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
     }
+    int kind = 0;
+    const afd::Coef k = afd::make_coef(spacing, K, dt, cond == AFD_COND_EXPONENTIAL, &kind);
+    return run_passes(ctx, in, out, nx, ny, nz, kind, k, n_iter);
+}
+
+// n_iter >= 1 passes of conductance kind `kind` with coefficients k.
+afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
+                      int64_t nz, int kind, const afd::Coef &k, int n_iter)
+{
+    const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
+    cudaError_t e = cudaSuccess;
     afd_status st = ensure_buffer(ctx, &ctx->scratch, &ctx->scratch_bytes, bytes);
     if (st != AFD_OK)
         return st;
-    int kind = 0;
-    const afd::Coef k = afd::make_coef(spacing, K, dt, cond == AFD_COND_EXPONENTIAL, &kind);
 
     const bool inplace = (in == out);
     auto dst_of = [&](int i) -> float * {
@@ -488,6 +500,39 @@ afd_status afd_filter_out(afd_ctx *ctx, const float *in, float *out, int64_t nx,
     if (st != AFD_OK)
         return st;
     return filter_device(ctx, in, out, nx, ny, nz, spacing, K, dt, n_iter, cond);
+}
+
+afd_status afd_filter_intensity(afd_ctx *ctx, const float *in, float *out, int64_t nx,
+                                int64_t ny, int64_t nz, const float *C, float K, float rms,
+                                float tau, int n_iter)
+{
+    if (!ctx || !in || !out || !C || !dims_ok(nx, ny, nz) || n_iter < 0)
+        return AFD_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!(C[a] >= 0.0f) || !std::isfinite(C[a]))
+            return AFD_EINVAL;
+    if (std::isnan(K) || K < 0.0f || std::isnan(rms) || rms < 0.0f || !(tau > 0.0f) ||
+        !std::isfinite(tau))
+        return AFD_EINVAL;
+    if (in != out) {
+        const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
+        const char *a = reinterpret_cast<const char *>(in);
+        const char *b = reinterpret_cast<const char *>(out);
+        if (a < b + bytes && b < a + bytes)
+            return AFD_EINVAL;
+    }
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    if (n_iter == 0 || K == 0.0f || rms == 0.0f) {  // S = 0: identity
+        cudaError_t e = cudaSuccess;
+        if (in != out)
+            e = cudaMemcpyAsync(out, in, static_cast<size_t>(nx * ny * nz) * sizeof(float),
+                                cudaMemcpyDeviceToDevice, ctx->stream);
+        return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+    }
+    const afd::Coef k = afd::make_coef_intensity(C, K, rms, tau);
+    return run_passes(ctx, in, out, nx, ny, nz, afd::COND_INT, k, n_iter);
 }
 
 afd_status afd_filter_host(afd_ctx *ctx, const float *host_in, float *host_out, int64_t nx,

@@ -49,8 +49,13 @@
 namespace afd {
 
 // Conductance kinds as the kernels see them.  LIN (g = 1) is what both
-// conductances become for K = +inf.
-enum CondKind : int { COND_EXP = 0, COND_RAT = 1, COND_LIN = 2 };
+// conductances become for K = +inf.  INT is the paper's intensity-driven form
+// (Sec. 3.3, the update after eq. "conductivepara"): linear face fluxes
+// G = tau C_a delta and one conductance per voxel,
+//     I' = I + S ((s_x + s_y) + s_z),  S = 1 / (1 + I^2 / (K rms)^2),
+// evaluated as I' = fma((s_x + s_y) + s_z, rcp(fma(ai, I*I, 1)), I) with
+// ai = 1/(K rms)^2.
+enum CondKind : int { COND_EXP = 0, COND_RAT = 1, COND_LIN = 2, COND_INT = 3 };
 
 // Per-call, per-axis coefficients (see above), computed on the host in double
 // and rounded once.
@@ -58,6 +63,7 @@ struct Coef {
     float ax, ay, az;
     float bx, by, bz;
     float nz;  // -0.0f (see above)
+    float ai;  // intensity form: 1/(K rms)^2 (unused otherwise)
 };
 
 // Host: coefficients for spacing h (NULL = unit), K > 0 (may be +inf), dt > 0.
@@ -100,6 +106,27 @@ inline Coef make_coef(const float *spacing, float K, float dt, bool cond_exponen
     c.by = static_cast<float>(B[1]);
     c.bz = static_cast<float>(B[2]);
     c.nz = -0.0f;
+    c.ai = 0.0f;
+    return c;
+}
+
+// Host: coefficients of the paper's intensity-driven form: face weights
+// tau C_a and ai = 1/(K rms)^2 (clamped to the float range; K rms = +inf gives
+// S = 1, the heat equation with weights tau C_a).
+inline Coef make_coef_intensity(const float *C, float K, float rms, float tau)
+{
+    Coef c;
+    const double t = static_cast<double>(tau);
+    c.ax = static_cast<float>(t * static_cast<double>(C[0]));
+    c.ay = static_cast<float>(t * static_cast<double>(C[1]));
+    c.az = static_cast<float>(t * static_cast<double>(C[2]));
+    c.bx = c.by = c.bz = 0.0f;
+    c.nz = -0.0f;
+    const double kr = static_cast<double>(K) * static_cast<double>(rms);
+    double ai = std::isinf(kr) ? 0.0 : 1.0 / (kr * kr);
+    if (!(ai <= static_cast<double>(std::numeric_limits<float>::max())))
+        ai = std::numeric_limits<float>::max();
+    c.ai = static_cast<float>(ai);
     return c;
 }
 
@@ -121,7 +148,7 @@ __device__ __forceinline__ float ex2_approx(float x)
 template <int C>
 __device__ __forceinline__ float face_flux(float delta, float A, float B, float Z)
 {
-    if (C == COND_LIN)
+    if (C == COND_LIN || C == COND_INT)
         return __fmaf_rn(A, delta, Z);
     const float t = __fmul_rn(delta, delta);
     const float u = __fmaf_rn(A, t, B);
@@ -137,6 +164,18 @@ __device__ __forceinline__ float pm_update(float c, float gxm, float gxp, float 
     const float sy = __fsub_rn(gyp, gym);
     const float sz = __fsub_rn(gzp, gzm);
     return __fadd_rn(c, __fadd_rn(__fadd_rn(sx, sy), sz));
+}
+
+// The intensity-driven update (COND_INT).
+__device__ __forceinline__ float pm_update_int(float c, float gxm, float gxp, float gym,
+                                               float gyp, float gzm, float gzp, float ai)
+{
+    const float sx = __fsub_rn(gxp, gxm);
+    const float sy = __fsub_rn(gyp, gym);
+    const float sz = __fsub_rn(gzp, gzm);
+    const float acc = __fadd_rn(__fadd_rn(sx, sy), sz);
+    const float S = rcp_approx(__fmaf_rn(ai, __fmul_rn(c, c), 1.0f));
+    return __fmaf_rn(acc, S, c);
 }
 
 // ---------------------------------------------------------------- packed ---
@@ -198,7 +237,7 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
 template <int C>
 __device__ __forceinline__ f2_t face_flux2(f2_t delta, f2_t A2, f2_t B2, f2_t Z2)
 {
-    if (C == COND_LIN)
+    if (C == COND_LIN || C == COND_INT)
         return f2_fma(A2, delta, Z2);
     const f2_t t = f2_mul(delta, delta);
     const f2_t u = f2_fma(A2, t, B2);
@@ -213,6 +252,28 @@ __device__ __forceinline__ f2_t face_flux2(f2_t delta, f2_t A2, f2_t B2, f2_t Z2
 __device__ __forceinline__ f2_t pm_update2(f2_t c, f2_t sx, f2_t sy, f2_t sz)
 {
     return f2_add(c, f2_add(f2_add(sx, sy), sz));
+}
+
+// Packed intensity-driven update of two voxels (pm_update_int on each lane);
+// ai2 and one2 hold ai and 1.0f in both lanes.
+__device__ __forceinline__ f2_t pm_update2_int(f2_t c, f2_t sx, f2_t sy, f2_t sz, f2_t ai2,
+                                               f2_t one2)
+{
+    const f2_t acc = f2_add(f2_add(sx, sy), sz);
+    const f2_t u = f2_fma(ai2, f2_mul(c, c), one2);
+    float ul, uh;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(ul), "=f"(uh) : "l"(u));
+    return f2_fma(acc, f2_pack(rcp_approx(ul), rcp_approx(uh)), c);
+}
+
+// The voxel update of conductance kind C.
+template <int C>
+__device__ __forceinline__ f2_t update2(f2_t c, f2_t sx, f2_t sy, f2_t sz, f2_t ai2, f2_t one2)
+{
+    if constexpr (C == COND_INT)
+        return pm_update2_int(c, sx, sy, sz, ai2, one2);
+    else
+        return pm_update2(c, sx, sy, sz);
 }
 
 }  // namespace afd

@@ -179,6 +179,7 @@ __global__ void batch_coef_kernel(BatchDesc *__restrict__ desc, int count, int b
     k.by = b1;
     k.bz = b2;
     k.nz = -0.0f;
+    k.ai = 0.0f;
     desc[c].coef = k;
     desc[c].K = K;
 }

@@ -36,7 +36,10 @@ __global__ void __launch_bounds__(256)
     const float gyp = face_flux<C>(__fsub_rn(yp, c), k.ay, k.by, k.nz);
     const float gzm = face_flux<C>(__fsub_rn(c, zm), k.az, k.bz, k.nz);
     const float gzp = face_flux<C>(__fsub_rn(zp, c), k.az, k.bz, k.nz);
-    out[p] = pm_update(c, gxm, gxp, gym, gyp, gzm, gzp);
+    if constexpr (C == COND_INT)
+        out[p] = pm_update_int(c, gxm, gxp, gym, gyp, gzm, gzp, k.ai);
+    else
+        out[p] = pm_update(c, gxm, gxp, gym, gyp, gzm, gzp);
 }
 
 cudaError_t launch_pm_simple(int cond, const float *in, float *out, int nx, int ny, int nz,
@@ -52,6 +55,9 @@ cudaError_t launch_pm_simple(int cond, const float *in, float *out, int nx, int 
         break;
     case COND_RAT:
         pm_step_simple<COND_RAT><<<grid, block, 0, stream>>>(in, out, nx, ny, nz, k);
+        break;
+    case COND_INT:
+        pm_step_simple<COND_INT><<<grid, block, 0, stream>>>(in, out, nx, ny, nz, k);
         break;
     default:
         pm_step_simple<COND_LIN><<<grid, block, 0, stream>>>(in, out, nx, ny, nz, k);

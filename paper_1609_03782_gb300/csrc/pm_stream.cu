@@ -138,7 +138,7 @@ __device__ __forceinline__ void stg_q(typename Store<S>::T *p, Q v)
 }
 
 struct Packed {
-    f2_t ax, ay, az, bx, by, bz, z;
+    f2_t ax, ay, az, bx, by, bz, z, ai, one;
 };
 
 // A quad that straddles the cube's x face (only its first m < 4 voxels are
@@ -341,10 +341,10 @@ __device__ __forceinline__ bool plane_step(const PlaneArgs<S> &a, const Packed &
     const Q sx1 = x_sums<C>(cx1, xl1, f2_hi(f4), k);
 
     // ---- update: I' = I + ((s_x + s_y) + s_z)
-    const Q o0 = {pm_update2(cur0.a, sx0.a, f2_sub(fmid.a, fdn.a), f2_sub(fa0.a, fb0.a)),
-                  pm_update2(cur0.b, sx0.b, f2_sub(fmid.b, fdn.b), f2_sub(fa0.b, fb0.b))};
-    const Q o1 = {pm_update2(cur1.a, sx1.a, f2_sub(fup.a, fmid.a), f2_sub(fa1.a, fb1.a)),
-                  pm_update2(cur1.b, sx1.b, f2_sub(fup.b, fmid.b), f2_sub(fa1.b, fb1.b))};
+    const Q o0 = {update2<C>(cur0.a, sx0.a, f2_sub(fmid.a, fdn.a), f2_sub(fa0.a, fb0.a), k.ai, k.one),
+                  update2<C>(cur0.b, sx0.b, f2_sub(fmid.b, fdn.b), f2_sub(fa0.b, fb0.b), k.ai, k.one)};
+    const Q o1 = {update2<C>(cur1.a, sx1.a, f2_sub(fup.a, fmid.a), f2_sub(fa1.a, fb1.a), k.ai, k.one),
+                  update2<C>(cur1.b, sx1.b, f2_sub(fup.b, fmid.b), f2_sub(fa1.b, fb1.b), k.ai, k.one)};
     typename Store<S>::T *po = a.out0 + static_cast<int64_t>(z) * a.ny * a.row_stride;
     if (a.act0)
         stg_q<S>(po, o0);
@@ -420,6 +420,8 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
         k.by = f2_pack(tc.k.by, tc.k.by);
         k.bz = f2_pack(tc.k.bz, tc.k.bz);
         k.z = f2_pack(tc.k.nz, tc.k.nz);
+        k.ai = f2_pack(tc.k.ai, tc.k.ai);
+        k.one = f2_pack(1.0f, 1.0f);
         const int x = tc.x0 + 4 * qx;
         const int ya = tc.y0 + 2 * ry;  // row 0
         const int yb = ya + 1;          // row 1
@@ -543,7 +545,11 @@ cudaError_t batch_attr()
 template <int S>
 cudaError_t stream_attr_all()
 {
-    cudaError_t e = stream_attr<S, COND_EXP>();
+    cudaError_t e = cudaSuccess;
+    if constexpr (S == STORE_F32)
+        e = stream_attr<S, COND_INT>();
+    if (e == cudaSuccess)
+        e = stream_attr<S, COND_EXP>();
     if (e == cudaSuccess)
         e = stream_attr<S, COND_RAT>();
     if (e == cudaSuccess)
@@ -639,6 +645,10 @@ template <int S>
 cudaError_t stream_launch_c(int cond, const CUtensorMap &tmap, void *out, int nx, int ny, int nz,
                             const Coef &k, const StreamPlan &plan, int *err, cudaStream_t stream)
 {
+    if constexpr (S == STORE_F32) {
+        if (cond == COND_INT)
+            return stream_launch<S, COND_INT>(tmap, out, nx, ny, nz, k, plan, err, stream);
+    }
     switch (cond) {
     case COND_EXP: return stream_launch<S, COND_EXP>(tmap, out, nx, ny, nz, k, plan, err, stream);
     case COND_RAT: return stream_launch<S, COND_RAT>(tmap, out, nx, ny, nz, k, plan, err, stream);
