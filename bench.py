@@ -58,9 +58,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["afd", "reference"], default="afd")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--lines", default="precision,batch,serving",
+    ap.add_argument("--lines", default="paper,precision,batch,serving",
                     help="extra lines measured after the headline (N=1 only): any of "
-                         "precision, batch, serving, or 'none'")
+                         "paper, precision, batch, serving, or 'none'")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="arrival window per request rate of the serving line")
     return ap.parse_args()
@@ -272,6 +272,47 @@ def line_precision(afd, ctx, cube, d_in, ref32, sig):
                      "value": best["value"]}, "rows": rows}
 
 
+def line_paper_form(afd, ctx):
+    """The paper's own benchmark: its intensity-driven filter with its defaults
+    (K = 1.5, tau = 0.0325, n = 20, C = 5) on a cube of the size of its
+    benchmark cube (N = 1.4e8 voxels); device-only and with the host <->
+    device copies the paper includes in its GPU timing."""
+    import torch
+    import synth
+    shape = (536, 512, 512)  # 1.405e8 voxels
+    cube = synth.galaxy_cube(shape, 0, 8, 2)
+    n_vox = cube.size
+    d_in = torch.from_numpy(cube).cuda()
+    d_out = torch.empty_like(d_in)
+    rms = afd.afd_noise_rms(ctx, d_in)
+    C = (5.0, 5.0, 5.0)
+    run = lambda: afd.afd_filter_intensity(ctx, d_in, d_out, 1.5, rms, 0.0325, 20, C)
+    run()
+    ms = _events_ms(run, 10)
+    h_in = torch.from_numpy(cube).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+
+    def e2e():
+        d_in.copy_(h_in, non_blocking=True)
+        afd.afd_filter_intensity(ctx, d_in, d_out, 1.5, rms, 0.0325, 20, C)
+        h_out.copy_(d_out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        e2e()
+    e_ms = (time.perf_counter() - t0) / 5 * 1e3
+    return {"unit": UNIT, "workload": "intensity-driven form, K = 1.5 (units of the GPU noise "
+            "rms), tau = 0.0325, n = 20, C = 5 (the paper's defaults), on a 512x512x536 "
+            "synthetic cube (1.41e8 voxels, the size of the paper's benchmark cube)",
+            "value": n_vox * 20 / (ms / 1e3) / 1e9, "ms": ms,
+            "e2e_value": n_vox * 20 / (e_ms / 1e3) / 1e9, "e2e_ms": e_ms,
+            "paper_context": {"gtx860m_opengl_incl_io_gvox_it_s": 0.90,
+                              "i7_8core_openmp_gvox_it_s": "0.036-0.050",
+                              "note": "other hardware, other data (NGC 2841); context only"}}
+
+
 def line_batch(afd, ctx):
     """300 galaxy cutouts of uneven size, K_i = 1.5 sigma_i (GPU FP64 noise
     estimate), 20 iterations, one CUDA-graph launch per call; z-chunk picked
@@ -477,6 +518,8 @@ def run_afd(args):
     lines = {}
     if rank == 0 and world == 1 and args.lines != "none":
         want = set(args.lines.split(","))
+        if "paper" in want:
+            lines["paper"] = line_paper_form(afd, ctx)
         if "precision" in want:
             lines["precision"] = line_precision(afd, ctx, cube, d_in, d_out, sig)
         if "batch" in want:
