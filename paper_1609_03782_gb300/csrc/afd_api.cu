@@ -242,8 +242,10 @@ afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int
         for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
             const float *src = src_of(i);
             const int m = (src == in) ? 0 : (src == out ? 1 : 2);
+            afd::StreamPlan pl = plan;
+            pl.rev = i & 1;  // start where the previous pass ended (L2)
             e = afd::launch_pm_stream(kind, maps[m], dst_of(i), static_cast<int>(nx),
-                                      static_cast<int>(ny), static_cast<int>(nz), k, plan,
+                                      static_cast<int>(ny), static_cast<int>(nz), k, pl,
                                       ctx->d_err, ctx->stream);
             ctx->launches++;
         }
@@ -699,10 +701,11 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
                                 static_cast<int>(ny), static_cast<int>(nz));
             if (st != AFD_OK)
                 return st;
-            const afd::StreamPlan plan =
+            afd::StreamPlan plan =
                 afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
                                     static_cast<int>(nz), ctx->sm_count, ctx->stream_bps,
                                     ctx->zc_hint);
+            plan.rev = i & 1;
             e = afd::launch_pm_stream_s(S, kind, map, dst_of(i), static_cast<int>(nx),
                                         static_cast<int>(ny), static_cast<int>(nz), k, plan,
                                         ctx->d_err, ctx->stream);

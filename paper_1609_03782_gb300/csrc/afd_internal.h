@@ -26,12 +26,20 @@ constexpr int kStreamSlots = AFD_STREAM_SLOTS;          // planes in the smem ri
 constexpr int kStreamMinBlocks = AFD_STREAM_MIN_BLOCKS; // CTAs per SM to fit
 constexpr int kStreamConsumerWarps = 8;
 constexpr int kStreamThreads = kStreamConsumerWarps * 32 + 32;  // + 1 producer warp
+// Registers per thread for kStreamMinBlocks CTAs per SM: the warps are spread
+// over the SM's four 16K-register quarters, so the quarter with the most
+// warps sets the limit (allocated in multiples of 8).
+constexpr int kStreamWarpsPerQuarter = (kStreamMinBlocks * (kStreamThreads / 32) + 3) / 4;
+constexpr int kStreamMaxRegs = 16384 / (32 * kStreamWarpsPerQuarter) / 8 * 8 > 248
+                                   ? 248
+                                   : 16384 / (32 * kStreamWarpsPerQuarter) / 8 * 8;
 
 struct StreamPlan {
-    int tiles_x, tiles_y, tiles_z;  // tile grid
-    int zc;                          // planes per z-chunk
+    int tiles_x, tiles_y, tiles_z;  // tile grid (tiles_z = number of z-chunks)
+    int zc;                          // planes of the longest z-chunk
     int64_t ntiles;
     int grid;                        // persistent CTAs
+    int rev;                         // take the tiles in reverse order (odd passes)
 };
 
 size_t pm_stream_smem_bytes();

@@ -63,19 +63,24 @@ struct TileCoord {
     int x0, y0, z0, z1, zlo, np;
 };
 
-__device__ __forceinline__ TileCoord decode_tile(int64_t t, int tiles_x, int tiles_y, int zc,
+// Tile t of a cube cut into tiles_x x tiles_y columns and z-chunks; t runs
+// over the columns fastest, so the CTAs of one round work on neighbouring
+// columns at the same depth (shared halos stay in L2).  The chunks are
+// zlen + 1 planes long for tz < zrem and zlen planes after that: lengths that
+// differ by at most one let the planner pick a chunk count that fills every
+// CTA's rounds.
+__device__ __forceinline__ TileCoord decode_tile(int t, int tiles_x, int txy, int zlen, int zrem,
                                                  int nz)
 {
-    const int64_t txy = static_cast<int64_t>(tiles_x) * tiles_y;
-    const int tz = static_cast<int>(t / txy);
-    const int r = static_cast<int>(t - static_cast<int64_t>(tz) * txy);
+    const int tz = t / txy;
+    const int r = t - tz * txy;
     const int ty = r / tiles_x;
     const int tx = r - ty * tiles_x;
     TileCoord c;
     c.x0 = tx * TX;
     c.y0 = ty * TY;
-    c.z0 = tz * zc;
-    c.z1 = min(c.z0 + zc, nz);
+    c.z0 = tz * zlen + min(tz, zrem);
+    c.z1 = c.z0 + zlen + (tz < zrem ? 1 : 0);
     c.zlo = max(c.z0 - 1, 0);
     const int zhi = min(c.z1, nz - 1);
     c.np = zhi - c.zlo + 1;
@@ -196,16 +201,20 @@ __device__ __forceinline__ void chunk_planes(int tz, int zc, int nz, int &z0, in
     np = min(z1, nz - 1) - zlo + 1;
 }
 
-// One cube, described by kernel parameters (dense rows: pitch nx).
+// One cube, described by kernel parameters (dense rows: pitch nx).  With
+// `rev` the tiles are taken in the opposite order: a pass then starts on the
+// chunks the previous pass wrote last, which are still in L2.
 template <int S>
 struct OneCube {
     const void *map;
     typename Store<S>::T *out;
-    int nx, ny, nz, tiles_x, tiles_y, zc;
+    int nx, ny, nz, tiles_x, txy, zlen, zrem;
+    int tlast;  // ntiles - 1 with `rev`, else 0 (tiles counted from the end)
     Coef k;
     __device__ __forceinline__ void tile(int64_t t, TileInfo<S> &ti) const
     {
-        const TileCoord tc = decode_tile(t, tiles_x, tiles_y, zc, nz);
+        const int tt = tlast > 0 ? tlast - static_cast<int>(t) : static_cast<int>(t);
+        const TileCoord tc = decode_tile(tt, tiles_x, txy, zlen, zrem, nz);
         ti.x0 = tc.x0;
         ti.y0 = tc.y0;
         ti.z0 = tc.z0;
@@ -495,17 +504,17 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
 
 
 template <int S, int C>
-__global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
+__global__ void __maxnreg__(kStreamMaxRegs)
     pm_step_stream(const __grid_constant__ CUtensorMap tmap, typename Store<S>::T *__restrict__ out,
-                   int nx, int ny, int nz, int tiles_x, int tiles_y, int zc, int64_t ntiles,
-                   Coef kc, int *err)
+                   int nx, int ny, int nz, int tiles_x, int txy, int zlen, int zrem, int ntiles,
+                   int tlast, Coef kc, int *err)
 {
-    const OneCube<S> src{&tmap, out, nx, ny, nz, tiles_x, tiles_y, zc, kc};
+    const OneCube<S> src{&tmap, out, nx, ny, nz, tiles_x, txy, zlen, zrem, tlast, kc};
     stream_body<S, C>(src, ntiles, err);
 }
 
 template <int S, int C>
-__global__ void __launch_bounds__(kStreamThreads, kStreamMinBlocks)
+__global__ void __maxnreg__(kStreamMaxRegs)
     pm_step_batch(const BatchDesc *__restrict__ desc, const int2 *__restrict__ list,
                   const int2 *__restrict__ roles, int64_t ntiles, int src_role, int dst_role,
                   int *err)
@@ -599,35 +608,37 @@ StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_s
     p.tiles_y = (ny + TY - 1) / TY;
     const int64_t txy = static_cast<int64_t>(p.tiles_x) * p.tiles_y;
     const int64_t gmax = static_cast<int64_t>(sm_count) * (blocks_per_sm > 0 ? blocks_per_sm : 1);
-    int zc = zc_hint;
-    if (zc <= 0) {
-        // Largest chunk that keeps the CTA slots busy: score = fraction of CTA
-        // slots doing work over the rounds x fraction of loaded planes that
-        // are not halo.
-        const int cand[4] = {64, 32, 16, 8};
+    int nzc;
+    if (zc_hint > 0) {
+        nzc = (nz + zc_hint - 1) / zc_hint;
+    } else {
+        // The busiest CTA's work decides the pass time: rounds x (longest
+        // chunk + the per-tile cost, measured at about one plane).  Take
+        // the chunk count that minimises it, the fewer tiles on a tie.
+        const int cmax = nz < 512 ? nz : 512;
         double best = -1.0;
-        zc = 8;
-        for (int i = 0; i < 4; ++i) {
-            const int c = cand[i];
-            const int64_t nt = txy * ((nz + c - 1) / c);
+        nzc = 1;
+        for (int c = 1; c <= cmax; ++c) {
+            const int64_t nt = txy * c;
             const int64_t rounds = (nt + gmax - 1) / gmax;
-            const double busy = static_cast<double>(nt) / static_cast<double>(rounds * gmax);
-            const int planes = c < nz ? c : nz;
-            const double halo = static_cast<double>(planes) / (planes + (nz > planes ? 2 : 0));
-            const double score = busy * halo;
-            if (score > best + 1e-9) {
-                best = score;
-                zc = c;
+            const int len = (nz + c - 1) / c;
+            const double cost = static_cast<double>(rounds) * (len + 1.0);
+            if (best < 0.0 || cost < best * (1.0 - 1e-3)) {
+                best = cost;
+                nzc = c;
             }
         }
     }
-    if (zc > nz)
-        zc = nz;
-    p.zc = zc;
-    p.tiles_z = (nz + zc - 1) / zc;
+    if (nzc > nz)
+        nzc = nz;
+    if (nzc < 1)
+        nzc = 1;
+    p.tiles_z = nzc;
+    p.zc = (nz + nzc - 1) / nzc;
     p.ntiles = txy * p.tiles_z;
     const int64_t rounds = (p.ntiles + gmax - 1) / gmax;
     p.grid = static_cast<int>((p.ntiles + rounds - 1) / rounds);
+    p.rev = 0;
     return p;
 }
 
@@ -637,8 +648,9 @@ cudaError_t stream_launch(const CUtensorMap &tmap, void *out, int nx, int ny, in
                           const Coef &k, const StreamPlan &plan, int *err, cudaStream_t stream)
 {
     pm_step_stream<S, C><<<plan.grid, kStreamThreads, pm_stream_smem_bytes(), stream>>>(
-        tmap, static_cast<typename Store<S>::T *>(out), nx, ny, nz, plan.tiles_x, plan.tiles_y,
-        plan.zc, plan.ntiles, k, err);
+        tmap, static_cast<typename Store<S>::T *>(out), nx, ny, nz, plan.tiles_x,
+        plan.tiles_x * plan.tiles_y, nz / plan.tiles_z, nz % plan.tiles_z,
+        static_cast<int>(plan.ntiles), plan.rev ? static_cast<int>(plan.ntiles) - 1 : 0, k, err);
     return cudaGetLastError();
 }
 template <int S>

@@ -85,7 +85,7 @@ def test_ragged_shapes_all_kernels(afd, ctx, shape, cond):
     a = run(afd, ctx, cube, 1.3, 0.1, n, cond, sp, kernel="simple")
     assert np.abs(a - ref).max() <= tol(n)
     if shape[2] % 4 == 0:
-        for zc in (0, 1, 3, 8):
+        for zc in (0, 1, 3, 5, 8):  # uneven chunk lengths where zc does not divide nz
             b = run(afd, ctx, cube, 1.3, 0.1, n, cond, sp, kernel="stream", zc=zc)
             assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), zc
 
