@@ -164,6 +164,14 @@ afd_status set_device(afd_ctx *ctx)
     return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
 }
 
+// Zero the streaming kernel's tile counter (stream-ordered) before a sequence
+// of launches.
+cudaError_t tiles_reset(afd_ctx *ctx)
+{
+    ctx->tiles_base = 0;
+    return cudaMemsetAsync(ctx->d_tiles, 0, sizeof(unsigned long long), ctx->stream);
+}
+
 // The iteration driver shared by afd_filter, afd_filter_out and
 // afd_filter_host.  Pass i reads src_i and writes dst_i, src_0 = in,
 // src_i = dst_{i-1}.  Out of place (in != out) the destinations alternate
@@ -239,14 +247,14 @@ afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int
         const afd::StreamPlan plan =
             afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny), static_cast<int>(nz),
                                 ctx->sm_count, ctx->stream_bps, ctx->zc_hint);
+        e = tiles_reset(ctx);
         for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
             const float *src = src_of(i);
             const int m = (src == in) ? 0 : (src == out ? 1 : 2);
-            afd::StreamPlan pl = plan;
-            pl.rev = i & 1;  // start where the previous pass ended (L2)
             e = afd::launch_pm_stream(kind, maps[m], dst_of(i), static_cast<int>(nx),
-                                      static_cast<int>(ny), static_cast<int>(nz), k, pl,
-                                      ctx->d_err, ctx->stream);
+                                      static_cast<int>(ny), static_cast<int>(nz), k, plan,
+                                      ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream);
+            ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
             ctx->launches++;
         }
     } else {
@@ -411,6 +419,7 @@ afd_status afd_create(afd_ctx **out, int device, void *cuda_stream)
         return st;
     }
     ctx->d_err = static_cast<int *>(p);
+    ctx->d_tiles = reinterpret_cast<unsigned long long *>(ctx->d_err + 16);
     ctx->d_out4 = reinterpret_cast<double *>(static_cast<char *>(p) + sizeof(int) * 32);
     ctx->d_part = ctx->d_out4 + 4;
     e = cudaMemset(ctx->d_err, 0, sizeof(int) * 32);
@@ -681,6 +690,7 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
     const bool fits = ((nx * es) % 16 == 0) && (reinterpret_cast<uintptr_t>(in) & 15u) == 0 &&
                       (reinterpret_cast<uintptr_t>(out) & 15u) == 0 && !std::isinf(K) &&
                       (reinterpret_cast<uintptr_t>(scr) & 15u) == 0;
+    bool tiles_zeroed = false;
     for (int i = 0; i < npass; ++i) {
         const int T = depth_of(i);
         if (fits && T == 1) {
@@ -701,14 +711,20 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
                                 static_cast<int>(ny), static_cast<int>(nz));
             if (st != AFD_OK)
                 return st;
-            afd::StreamPlan plan =
+            const afd::StreamPlan plan =
                 afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
                                     static_cast<int>(nz), ctx->sm_count, ctx->stream_bps,
                                     ctx->zc_hint);
-            plan.rev = i & 1;
-            e = afd::launch_pm_stream_s(S, kind, map, dst_of(i), static_cast<int>(nx),
-                                        static_cast<int>(ny), static_cast<int>(nz), k, plan,
-                                        ctx->d_err, ctx->stream);
+            if (!tiles_zeroed) {
+                e = tiles_reset(ctx);
+                tiles_zeroed = true;
+            }
+            if (e == cudaSuccess)
+                e = afd::launch_pm_stream_s(S, kind, map, dst_of(i), static_cast<int>(nx),
+                                            static_cast<int>(ny), static_cast<int>(nz), k, plan,
+                                            ctx->d_tiles, ctx->tiles_base, ctx->d_err,
+                                            ctx->stream);
+            ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
             ctx->launches++;
             if (e != cudaSuccess)
                 return cuda_fail(ctx, e);

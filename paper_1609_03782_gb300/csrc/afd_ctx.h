@@ -17,6 +17,8 @@ struct afd_ctx {
     int zc_hint = 0;             // streaming kernel z-chunk override (0 = auto)
     afd_kernel kernel = AFD_KERNEL_AUTO;
     int *d_err = nullptr;        // device error word (bounded-wait expiries)
+    unsigned long long *d_tiles = nullptr;  // streaming kernel tile counter (in d_err's block)
+    unsigned long long tiles_base = 0;      // counter value at the next launch's start
     float *scratch = nullptr;    // ping-pong partner buffer
     size_t scratch_bytes = 0;
     float *stage = nullptr;      // device copy for afd_filter_host

@@ -34,24 +34,40 @@ constexpr int kStreamMaxRegs = 16384 / (32 * kStreamWarpsPerQuarter) / 8 * 8 > 2
                                    ? 248
                                    : 16384 / (32 * kStreamWarpsPerQuarter) / 8 * 8;
 
+// z-chunks of the streaming kernel: nuni chunks of zlen (+1 for the first
+// zrem) planes from z = 0, then nlev chunks starting at off[0..nlev-1] (and
+// off[nlev] = nz).
+constexpr int kStreamMaxLevels = 64;
+struct ZLevels {
+    int nuni, zlen, zrem;
+    int nlev;
+    int off[kStreamMaxLevels + 1];
+};
+
 struct StreamPlan {
     int tiles_x, tiles_y, tiles_z;  // tile grid (tiles_z = number of z-chunks)
     int zc;                          // planes of the longest z-chunk
     int64_t ntiles;
     int grid;                        // persistent CTAs
-    int rev;                         // take the tiles in reverse order (odd passes)
+    ZLevels lv;
 };
+
+// Tiles are handed out through a 64-bit counter in device memory: zero it
+// (cudaMemsetAsync) before a sequence of launches, pass base = the sum of
+// ntiles of the launches before this one in the sequence.
 
 size_t pm_stream_smem_bytes();
 cudaError_t pm_stream_prepare();  // one-time kernel attributes
 cudaError_t pm_stream_occupancy(int *blocks_per_sm);
 StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_sm, int zc_hint);
 cudaError_t launch_pm_stream(int cond, const CUtensorMap &tmap_in, float *out, int nx, int ny,
-                             int nz, const Coef &k, const StreamPlan &plan, int *err,
+                             int nz, const Coef &k, const StreamPlan &plan,
+                             unsigned long long *ctr, unsigned long long base, int *err,
                              cudaStream_t stream);
 // Any storage kind (StoreKind); the map's box is pm_stream_box(S, ...).
 cudaError_t launch_pm_stream_s(int S, int cond, const CUtensorMap &tmap_in, void *out, int nx,
-                               int ny, int nz, const Coef &k, const StreamPlan &plan, int *err,
+                               int ny, int nz, const Coef &k, const StreamPlan &plan,
+                               unsigned long long *ctr, unsigned long long base, int *err,
                                cudaStream_t stream);
 void pm_stream_box(int S, int *box_w, int *box_h, int *hx);
 

@@ -38,11 +38,13 @@ constexpr int kMaxDevices = 64;
 // Shared by every call on a device; keeps the last call's contents.
 __device__ __align__(256) float g_noalloc_scratch[kMaxVoxels];
 __device__ __align__(256) int g_noalloc_err[64];
+__device__ __align__(8) unsigned long long g_noalloc_tiles[1];  // streaming kernel tile counter
 
 struct DeviceSetup {
     bool ready = false;
     float *scratch = nullptr;  // device address of g_noalloc_scratch
     int *err = nullptr;        // device address of g_noalloc_err
+    unsigned long long *tiles = nullptr;  // device address of g_noalloc_tiles
     int sm_count = 0;
     int stream_bps = 0;
 };
@@ -65,6 +67,9 @@ afd_status setup_device(int dev, DeviceSetup *out)
         if (cudaGetSymbolAddress(&p, g_noalloc_err) != cudaSuccess)
             return AFD_ECUDA;
         s.err = static_cast<int *>(p);
+        if (cudaGetSymbolAddress(&p, g_noalloc_tiles) != cudaSuccess)
+            return AFD_ECUDA;
+        s.tiles = static_cast<unsigned long long *>(p);
         if (cudaDeviceGetAttribute(&s.sm_count, cudaDevAttrMultiProcessorCount, dev) !=
             cudaSuccess)
             return AFD_ECUDA;
@@ -179,13 +184,14 @@ extern "C" afd_status afd_filter_noalloc(const float *in, float *out, int64_t nx
                 return AFD_ECUDA;
         const afd::StreamPlan plan = afd::pm_stream_plan(inx, iny, inz, s.sm_count,
                                                          s.stream_bps, 0);
+        e = cudaMemsetAsync(s.tiles, 0, sizeof(unsigned long long), stream);
+        unsigned long long base = 0;
         for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
             const float *src = src_of(i);
             const int m = (src == in) ? 0 : (src == out ? 1 : 2);
-            afd::StreamPlan pl = plan;
-            pl.rev = i & 1;
-            e = afd::launch_pm_stream(kind, maps[m], dst_of(i), inx, iny, inz, k, pl, s.err,
-                                      stream);
+            e = afd::launch_pm_stream(kind, maps[m], dst_of(i), inx, iny, inz, k, plan, s.tiles,
+                                      base, s.err, stream);
+            base += static_cast<unsigned long long>(plan.ntiles);
         }
     } else {
         for (int i = 0; i < n_iter && e == cudaSuccess; ++i)

@@ -64,12 +64,12 @@ struct TileCoord {
 };
 
 // Tile t of a cube cut into tiles_x x tiles_y columns and z-chunks; t runs
-// over the columns fastest, so the CTAs of one round work on neighbouring
-// columns at the same depth (shared halos stay in L2).  The chunks are
-// zlen + 1 planes long for tz < zrem and zlen planes after that: lengths that
-// differ by at most one let the planner pick a chunk count that fills every
-// CTA's rounds.
-__device__ __forceinline__ TileCoord decode_tile(int t, int tiles_x, int txy, int zlen, int zrem,
+// over the columns fastest, so the CTAs working at one time are on
+// neighbouring columns at the same depth (shared halos stay in L2).  The
+// first lv.nuni chunks are zlen + 1 planes long for tz < zrem and zlen planes
+// after that; the chunks after them start at lv.off[tz - nuni] (the guided
+// sequence of the planner, long chunks first and short ones last).
+__device__ __forceinline__ TileCoord decode_tile(int t, int tiles_x, int txy, const ZLevels &lv,
                                                  int nz)
 {
     const int tz = t / txy;
@@ -79,8 +79,13 @@ __device__ __forceinline__ TileCoord decode_tile(int t, int tiles_x, int txy, in
     TileCoord c;
     c.x0 = tx * TX;
     c.y0 = ty * TY;
-    c.z0 = tz * zlen + min(tz, zrem);
-    c.z1 = c.z0 + zlen + (tz < zrem ? 1 : 0);
+    if (tz < lv.nuni) {
+        c.z0 = tz * lv.zlen + min(tz, lv.zrem);
+        c.z1 = c.z0 + lv.zlen + (tz < lv.zrem ? 1 : 0);
+    } else {
+        c.z0 = lv.off[tz - lv.nuni];
+        c.z1 = lv.off[tz - lv.nuni + 1];
+    }
     c.zlo = max(c.z0 - 1, 0);
     const int zhi = min(c.z1, nz - 1);
     c.np = zhi - c.zlo + 1;
@@ -201,20 +206,23 @@ __device__ __forceinline__ void chunk_planes(int tz, int zc, int nz, int &z0, in
     np = min(z1, nz - 1) - zlo + 1;
 }
 
-// One cube, described by kernel parameters (dense rows: pitch nx).  With
-// `rev` the tiles are taken in the opposite order: a pass then starts on the
-// chunks the previous pass wrote last, which are still in L2.
+// One cube, described by kernel parameters (dense rows: pitch nx).  Tiles
+// are handed out dynamically: a CTA starts on tile blockIdx.x and then takes
+// gridDim.x + (the next value of the launch's tile counter - base), so CTAs
+// on faster SMs take more tiles and all of them end within one short tile of
+// each other.
 template <int S>
 struct OneCube {
     const void *map;
     typename Store<S>::T *out;
-    int nx, ny, nz, tiles_x, txy, zlen, zrem;
-    int tlast;  // ntiles - 1 with `rev`, else 0 (tiles counted from the end)
+    int nx, ny, nz, tiles_x, txy;
+    const ZLevels *lv;
+    unsigned long long *ctr;
+    unsigned long long base;
     Coef k;
-    __device__ __forceinline__ void tile(int64_t t, TileInfo<S> &ti) const
+    __device__ __forceinline__ void tile(int t, TileInfo<S> &ti) const
     {
-        const int tt = tlast > 0 ? tlast - static_cast<int>(t) : static_cast<int>(t);
-        const TileCoord tc = decode_tile(tt, tiles_x, txy, zlen, zrem, nz);
+        const TileCoord tc = decode_tile(t, tiles_x, txy, *lv, nz);
         ti.x0 = tc.x0;
         ti.y0 = tc.y0;
         ti.z0 = tc.z0;
@@ -229,6 +237,11 @@ struct OneCube {
         ti.out = out;
         ti.k = k;
     }
+    __device__ __forceinline__ int64_t next(int64_t) const
+    {
+        return static_cast<int64_t>(gridDim.x) +
+               static_cast<int64_t>(atomicAdd(ctr, 1ull) - base);
+    }
 };
 
 // Many cubes of a resident batch: per-cube descriptors in global memory and a
@@ -240,6 +253,7 @@ struct ManyCubes {
     const int2 *list;
     const int2 *roles;
     int src, dst;
+    __device__ __forceinline__ int64_t next(int64_t t) const { return t + gridDim.x; }
     __device__ __forceinline__ void tile(int64_t t, TileInfo<S> &ti) const
     {
         const int2 ct = list[t];
@@ -376,6 +390,8 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
     unsigned char *slots = smem;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + NSLOT * SLOT_BYTES_MAX);
     uint64_t *empty = full + NSLOT;
+    // tile index of the tile whose first plane a slot holds, -1: no more tiles
+    int *tile_of = reinterpret_cast<int *>(empty + NSLOT);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -392,18 +408,31 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
         // ---------------- producer ----------------
         if (lane == 0) {
             uint32_t kk = 0;
-            for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            int64_t t = blockIdx.x;
+            for (;;) {
+                const bool more = t >= 0 && t < ntiles;
                 TileInfo<S> tc;
-                src.tile(t, tc);
-                for (int j = 0; j < tc.np; ++j, ++kk) {
+                if (more)
+                    src.tile(t, tc);
+                const int np = more ? tc.np : 1;
+                for (int j = 0; j < np; ++j, ++kk) {
                     const uint32_t slot = kk & (NSLOT - 1);
                     const uint32_t use = kk / NSLOT;
                     if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1u, err, kErrWaitEmpty))
                         return;
+                    if (j == 0)
+                        tile_of[slot] = more ? static_cast<int>(t) : -1;
+                    if (!more) {
+                        mbar_arrive(&full[slot]);  // the end mark: no data
+                        break;
+                    }
                     mbar_arrive_expect_tx(&full[slot], SL::BOX_BYTES);
                     tma_load_3d(slots + slot * SLOT_BYTES_MAX, tc.map, tc.x0 - SL::HX, tc.y0 - 1,
                                 tc.zlo + j, &full[slot]);
                 }
+                if (!more)
+                    break;
+                t = src.next(t);
             }
         }
         return;
@@ -417,7 +446,13 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
     const int cen1 = cen0 + SL::PX;                  // quad of row 1
     uint32_t kk = 0;
 
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (;;) {
+        // the next tile's first slot names the tile (or ends the loop)
+        if (!mbar_wait(&full[kk & (NSLOT - 1)], (kk / NSLOT) & 1u, err, kErrWaitFull))
+            return;
+        const int t = tile_of[kk & (NSLOT - 1)];
+        if (t < 0)
+            break;
         TileInfo<S> tc;
         src.tile(t, tc);
         const int nx = tc.nx, ny = tc.ny, nz = tc.nz;
@@ -506,10 +541,10 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
 template <int S, int C>
 __global__ void __maxnreg__(kStreamMaxRegs)
     pm_step_stream(const __grid_constant__ CUtensorMap tmap, typename Store<S>::T *__restrict__ out,
-                   int nx, int ny, int nz, int tiles_x, int txy, int zlen, int zrem, int ntiles,
-                   int tlast, Coef kc, int *err)
+                   int nx, int ny, int nz, int tiles_x, int txy, const __grid_constant__ ZLevels lv,
+                   int ntiles, unsigned long long *ctr, unsigned long long base, Coef kc, int *err)
 {
-    const OneCube<S> src{&tmap, out, nx, ny, nz, tiles_x, txy, zlen, zrem, tlast, kc};
+    const OneCube<S> src{&tmap, out, nx, ny, nz, tiles_x, txy, &lv, ctr, base, kc};
     stream_body<S, C>(src, ntiles, err);
 }
 
@@ -527,7 +562,8 @@ __global__ void __maxnreg__(kStreamMaxRegs)
 
 size_t pm_stream_smem_bytes()
 {
-    return static_cast<size_t>(NSLOT) * SLOT_BYTES_MAX + 2 * NSLOT * sizeof(uint64_t) + 128;
+    return static_cast<size_t>(NSLOT) * SLOT_BYTES_MAX + 2 * NSLOT * sizeof(uint64_t) +
+           NSLOT * sizeof(int) + 128;
 }
 
 void pm_stream_box(int S, int *box_w, int *box_h, int *hx)
@@ -601,6 +637,34 @@ cudaError_t pm_stream_occupancy(int *blocks_per_sm)
     return e;
 }
 
+namespace {
+// Guided z-chunks: each chunk is at most the share of the remaining work that
+// keeps every CTA busy while the CTAs that took the chunk's tiles finish them
+// (length <= remaining x txy / (grid + txy)), between lmin and 64 planes; the
+// last chunks are the shortest, so the CTAs end within one short tile of each
+// other.  Returns the number of chunks (-1: more than kStreamMaxLevels).
+int guided_levels(int nz, int64_t txy, int64_t grid, int lmin, int *off)
+{
+    int n = 0, z = 0;
+    while (z < nz) {
+        if (n >= kStreamMaxLevels)
+            return -1;
+        const int64_t left = nz - z;
+        int64_t len = left * txy / (grid + txy);
+        if (len < lmin)
+            len = lmin;
+        if (len > 64)
+            len = 64;
+        if (len > left || left - len < (lmin + 1) / 2)
+            len = left;
+        off[n++] = z;
+        z += static_cast<int>(len);
+    }
+    off[n] = nz;
+    return n;
+}
+}  // namespace
+
 StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_sm, int zc_hint)
 {
     StreamPlan p;
@@ -608,80 +672,88 @@ StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_s
     p.tiles_y = (ny + TY - 1) / TY;
     const int64_t txy = static_cast<int64_t>(p.tiles_x) * p.tiles_y;
     const int64_t gmax = static_cast<int64_t>(sm_count) * (blocks_per_sm > 0 ? blocks_per_sm : 1);
-    int nzc;
-    if (zc_hint > 0) {
-        nzc = (nz + zc_hint - 1) / zc_hint;
+    ZLevels &lv = p.lv;
+    lv.nuni = 0;
+    lv.zlen = 1;
+    lv.zrem = 0;
+    lv.nlev = 0;
+    lv.off[0] = 0;
+    int n = -1;
+    if (zc_hint <= 0)
+        for (int lmin = 8; n < 0; lmin *= 2)
+            n = guided_levels(nz, txy, gmax, lmin, lv.off);
+    if (n > 0) {
+        lv.nlev = n;
+        p.zc = 0;
+        for (int i = 0; i < n; ++i)
+            p.zc = max(p.zc, lv.off[i + 1] - lv.off[i]);
     } else {
-        // The busiest CTA's work decides the pass time: rounds x (longest
-        // chunk + the per-tile cost, measured at about one plane).  Take
-        // the chunk count that minimises it, the fewer tiles on a tie.
-        const int cmax = nz < 512 ? nz : 512;
-        double best = -1.0;
-        nzc = 1;
-        for (int c = 1; c <= cmax; ++c) {
-            const int64_t nt = txy * c;
-            const int64_t rounds = (nt + gmax - 1) / gmax;
-            const int len = (nz + c - 1) / c;
-            const double cost = static_cast<double>(rounds) * (len + 1.0);
-            if (best < 0.0 || cost < best * (1.0 - 1e-3)) {
-                best = cost;
-                nzc = c;
-            }
-        }
+        // a fixed z-chunk: chunks of equal length (+-1), none above zc_hint
+        const int zc = zc_hint > 0 ? zc_hint : nz;
+        lv.nuni = (nz + zc - 1) / zc;
+        lv.zlen = nz / lv.nuni;
+        lv.zrem = nz % lv.nuni;
+        lv.off[0] = nz;
+        p.zc = lv.zlen + (lv.zrem ? 1 : 0);
     }
-    if (nzc > nz)
-        nzc = nz;
-    if (nzc < 1)
-        nzc = 1;
-    p.tiles_z = nzc;
-    p.zc = (nz + nzc - 1) / nzc;
+    p.tiles_z = lv.nuni + lv.nlev;
     p.ntiles = txy * p.tiles_z;
-    const int64_t rounds = (p.ntiles + gmax - 1) / gmax;
-    p.grid = static_cast<int>((p.ntiles + rounds - 1) / rounds);
-    p.rev = 0;
+    p.grid = static_cast<int>(p.ntiles < gmax ? p.ntiles : gmax);
     return p;
 }
 
 namespace {
 template <int S, int C>
 cudaError_t stream_launch(const CUtensorMap &tmap, void *out, int nx, int ny, int nz,
-                          const Coef &k, const StreamPlan &plan, int *err, cudaStream_t stream)
+                          const Coef &k, const StreamPlan &plan, unsigned long long *ctr,
+                          unsigned long long base, int *err, cudaStream_t stream)
 {
+    if (plan.ntiles > 0x7fffffff)
+        return cudaErrorInvalidValue;
     pm_step_stream<S, C><<<plan.grid, kStreamThreads, pm_stream_smem_bytes(), stream>>>(
         tmap, static_cast<typename Store<S>::T *>(out), nx, ny, nz, plan.tiles_x,
-        plan.tiles_x * plan.tiles_y, nz / plan.tiles_z, nz % plan.tiles_z,
-        static_cast<int>(plan.ntiles), plan.rev ? static_cast<int>(plan.ntiles) - 1 : 0, k, err);
+        plan.tiles_x * plan.tiles_y, plan.lv, static_cast<int>(plan.ntiles), ctr, base, k, err);
     return cudaGetLastError();
 }
 template <int S>
 cudaError_t stream_launch_c(int cond, const CUtensorMap &tmap, void *out, int nx, int ny, int nz,
-                            const Coef &k, const StreamPlan &plan, int *err, cudaStream_t stream)
+                            const Coef &k, const StreamPlan &plan, unsigned long long *ctr,
+                            unsigned long long base, int *err, cudaStream_t stream)
 {
     if constexpr (S == STORE_F32) {
         if (cond == COND_INT)
-            return stream_launch<S, COND_INT>(tmap, out, nx, ny, nz, k, plan, err, stream);
+            return stream_launch<S, COND_INT>(tmap, out, nx, ny, nz, k, plan, ctr, base, err,
+                                              stream);
     }
     switch (cond) {
-    case COND_EXP: return stream_launch<S, COND_EXP>(tmap, out, nx, ny, nz, k, plan, err, stream);
-    case COND_RAT: return stream_launch<S, COND_RAT>(tmap, out, nx, ny, nz, k, plan, err, stream);
-    default: return stream_launch<S, COND_LIN>(tmap, out, nx, ny, nz, k, plan, err, stream);
+    case COND_EXP:
+        return stream_launch<S, COND_EXP>(tmap, out, nx, ny, nz, k, plan, ctr, base, err, stream);
+    case COND_RAT:
+        return stream_launch<S, COND_RAT>(tmap, out, nx, ny, nz, k, plan, ctr, base, err, stream);
+    default:
+        return stream_launch<S, COND_LIN>(tmap, out, nx, ny, nz, k, plan, ctr, base, err, stream);
     }
 }
 }  // namespace
 
 cudaError_t launch_pm_stream_s(int S, int cond, const CUtensorMap &tmap_in, void *out, int nx,
-                               int ny, int nz, const Coef &k, const StreamPlan &plan, int *err,
+                               int ny, int nz, const Coef &k, const StreamPlan &plan,
+                               unsigned long long *ctr, unsigned long long base, int *err,
                                cudaStream_t stream)
 {
     switch (S) {
     case STORE_F32:
-        return stream_launch_c<STORE_F32>(cond, tmap_in, out, nx, ny, nz, k, plan, err, stream);
+        return stream_launch_c<STORE_F32>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base, err,
+                                          stream);
     case STORE_F16:
-        return stream_launch_c<STORE_F16>(cond, tmap_in, out, nx, ny, nz, k, plan, err, stream);
+        return stream_launch_c<STORE_F16>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base, err,
+                                          stream);
     case STORE_BF16:
-        return stream_launch_c<STORE_BF16>(cond, tmap_in, out, nx, ny, nz, k, plan, err, stream);
+        return stream_launch_c<STORE_BF16>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base,
+                                           err, stream);
     default:
-        return stream_launch_c<STORE_I16>(cond, tmap_in, out, nx, ny, nz, k, plan, err, stream);
+        return stream_launch_c<STORE_I16>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base, err,
+                                          stream);
     }
 }
 
@@ -731,10 +803,12 @@ cudaError_t launch_pm_batch(int S, int cond, const BatchDesc *desc, const int2 *
 }
 
 cudaError_t launch_pm_stream(int cond, const CUtensorMap &tmap_in, float *out, int nx, int ny,
-                             int nz, const Coef &k, const StreamPlan &plan, int *err,
+                             int nz, const Coef &k, const StreamPlan &plan,
+                             unsigned long long *ctr, unsigned long long base, int *err,
                              cudaStream_t stream)
 {
-    return launch_pm_stream_s(STORE_F32, cond, tmap_in, out, nx, ny, nz, k, plan, err, stream);
+    return launch_pm_stream_s(STORE_F32, cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base, err,
+                              stream);
 }
 
 }  // namespace afd
