@@ -251,8 +251,10 @@ afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int
         for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
             const float *src = src_of(i);
             const int m = (src == in) ? 0 : (src == out ? 1 : 2);
+            afd::StreamPlan pl = plan;
+            pl.pdl = i > 0;
             e = afd::launch_pm_stream(kind, maps[m], dst_of(i), static_cast<int>(nx),
-                                      static_cast<int>(ny), static_cast<int>(nz), k, plan,
+                                      static_cast<int>(ny), static_cast<int>(nz), k, pl,
                                       ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream);
             ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
             ctx->launches++;
@@ -691,6 +693,7 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
                       (reinterpret_cast<uintptr_t>(out) & 15u) == 0 && !std::isinf(K) &&
                       (reinterpret_cast<uintptr_t>(scr) & 15u) == 0;
     bool tiles_zeroed = false;
+    bool prev_stream = false;  // the previous pass was a streaming-kernel launch
     for (int i = 0; i < npass; ++i) {
         const int T = depth_of(i);
         if (fits && T == 1) {
@@ -711,10 +714,12 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
                                 static_cast<int>(ny), static_cast<int>(nz));
             if (st != AFD_OK)
                 return st;
-            const afd::StreamPlan plan =
+            afd::StreamPlan plan =
                 afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
                                     static_cast<int>(nz), ctx->sm_count, ctx->stream_bps,
                                     ctx->zc_hint);
+            plan.pdl = prev_stream;
+            prev_stream = true;
             if (!tiles_zeroed) {
                 e = tiles_reset(ctx);
                 tiles_zeroed = true;
@@ -745,12 +750,14 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
             e = afd::tb_launch(S, T, kind, map, dst_of(i), static_cast<int>(nx),
                                static_cast<int>(ny), static_cast<int>(nz), k, plan, ctx->d_err,
                                ctx->stream);
+            prev_stream = false;
             ctx->launches++;
             if (e != cudaSuccess)
                 return cuda_fail(ctx, e);
         } else {
             st = fallback_pass(ctx, S, units, src_of(i), dst_of(i), nx, ny, nz, spacing, K, dt, T,
                                cond);
+            prev_stream = false;
             if (st != AFD_OK)
                 return st;
         }

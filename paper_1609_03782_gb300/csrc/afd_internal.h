@@ -50,6 +50,10 @@ struct StreamPlan {
     int64_t ntiles;
     int grid;                        // persistent CTAs
     ZLevels lv;
+    // launch as a programmatic dependent of the previous kernel in the stream
+    // (only when that kernel is a streaming pass: its CTAs then overlap that
+    // pass's last tiles)
+    bool pdl;
 };
 
 // Tiles are handed out through a 64-bit counter in device memory: zero it

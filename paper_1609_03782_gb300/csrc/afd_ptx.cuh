@@ -106,4 +106,17 @@ __device__ __forceinline__ void tma_load_3d(void *smem_dst, const void *tmap, in
         : "memory");
 }
 
+// Programmatic dependent launch (sm_90+): wait until the grids this one
+// depends on have completed and their memory is visible (a no-op when the
+// grid was not launched as a programmatic dependent), and let the next grid
+// in the stream be scheduled before this one ends.
+__device__ __forceinline__ void grid_dep_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 }  // namespace afd

@@ -189,7 +189,9 @@ extern "C" afd_status afd_filter_noalloc(const float *in, float *out, int64_t nx
         for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
             const float *src = src_of(i);
             const int m = (src == in) ? 0 : (src == out ? 1 : 2);
-            e = afd::launch_pm_stream(kind, maps[m], dst_of(i), inx, iny, inz, k, plan, s.tiles,
+            afd::StreamPlan pl = plan;
+            pl.pdl = i > 0;
+            e = afd::launch_pm_stream(kind, maps[m], dst_of(i), inx, iny, inz, k, pl, s.tiles,
                                       base, s.err, stream);
             base += static_cast<unsigned long long>(plan.ntiles);
         }

@@ -407,6 +407,12 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
     if (warp == NCW) {
         // ---------------- producer ----------------
         if (lane == 0) {
+            // Launched as a programmatic dependent of the previous pass, the
+            // CTA may start while that pass is still running: every global
+            // access of this CTA (the producer's loads and tile fetches, and
+            // the consumers' stores, which follow the loads) waits here until
+            // the previous grid has completed and its writes are visible.
+            grid_dep_wait();
             uint32_t kk = 0;
             int64_t t = blockIdx.x;
             for (;;) {
@@ -544,6 +550,7 @@ __global__ void __maxnreg__(kStreamMaxRegs)
                    int nx, int ny, int nz, int tiles_x, int txy, const __grid_constant__ ZLevels lv,
                    int ntiles, unsigned long long *ctr, unsigned long long base, Coef kc, int *err)
 {
+    grid_dep_launch_dependents();  // the next pass may take SMs as this one frees them
     const OneCube<S> src{&tmap, out, nx, ny, nz, tiles_x, txy, &lv, ctr, base, kc};
     stream_body<S, C>(src, ntiles, err);
 }
@@ -640,7 +647,7 @@ cudaError_t pm_stream_occupancy(int *blocks_per_sm)
 namespace {
 // Guided z-chunks: each chunk is at most the share of the remaining work that
 // keeps every CTA busy while the CTAs that took the chunk's tiles finish them
-// (length <= remaining x txy / (grid + txy)), between lmin and 64 planes; the
+// (length <= remaining x txy / (grid + txy)), between lmin and 32 planes; the
 // last chunks are the shortest, so the CTAs end within one short tile of each
 // other.  Returns the number of chunks (-1: more than kStreamMaxLevels).
 int guided_levels(int nz, int64_t txy, int64_t grid, int lmin, int *off)
@@ -653,8 +660,8 @@ int guided_levels(int nz, int64_t txy, int64_t grid, int lmin, int *off)
         int64_t len = left * txy / (grid + txy);
         if (len < lmin)
             len = lmin;
-        if (len > 64)
-            len = 64;
+        if (len > 32)
+            len = 32;
         if (len > left || left - len < (lmin + 1) / 2)
             len = left;
         off[n++] = z;
@@ -680,7 +687,7 @@ StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_s
     lv.off[0] = 0;
     int n = -1;
     if (zc_hint <= 0)
-        for (int lmin = 8; n < 0; lmin *= 2)
+        for (int lmin = 4; n < 0; lmin *= 2)
             n = guided_levels(nz, txy, gmax, lmin, lv.off);
     if (n > 0) {
         lv.nlev = n;
@@ -699,6 +706,7 @@ StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_s
     p.tiles_z = lv.nuni + lv.nlev;
     p.ntiles = txy * p.tiles_z;
     p.grid = static_cast<int>(p.ntiles < gmax ? p.ntiles : gmax);
+    p.pdl = false;
     return p;
 }
 
@@ -710,10 +718,20 @@ cudaError_t stream_launch(const CUtensorMap &tmap, void *out, int nx, int ny, in
 {
     if (plan.ntiles > 0x7fffffff)
         return cudaErrorInvalidValue;
-    pm_step_stream<S, C><<<plan.grid, kStreamThreads, pm_stream_smem_bytes(), stream>>>(
-        tmap, static_cast<typename Store<S>::T *>(out), nx, ny, nz, plan.tiles_x,
-        plan.tiles_x * plan.tiles_y, plan.lv, static_cast<int>(plan.ntiles), ctr, base, k, err);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(plan.grid));
+    cfg.blockDim = dim3(kStreamThreads);
+    cfg.dynamicSmemBytes = pm_stream_smem_bytes();
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = plan.pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, pm_step_stream<S, C>, tmap,
+                              static_cast<typename Store<S>::T *>(out), nx, ny, nz, plan.tiles_x,
+                              plan.tiles_x * plan.tiles_y, plan.lv, static_cast<int>(plan.ntiles),
+                              ctr, base, k, err);
 }
 template <int S>
 cudaError_t stream_launch_c(int cond, const CUtensorMap &tmap, void *out, int nx, int ny, int nz,
