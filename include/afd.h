@@ -102,9 +102,12 @@ afd_status afd_set_stream(afd_ctx *ctx, void *cuda_stream);
  * AFD_EINVAL.  All kernels give bit-identical results. */
 afd_status afd_set_kernel(afd_ctx *ctx, afd_kernel kernel);
 
-/* Tuning knob of the streaming kernel: the number of z planes one CTA
- * streams per tile (0 = choose automatically from the cube shape and the
- * device's SM count).  Results do not depend on it.  AFD_EINVAL if zc < 0. */
+/* Tuning knob of the streaming kernel: the largest number of z planes one
+ * CTA streams per tile; the cube is cut into chunks of equal length (+-1)
+ * no longer than zc.  0 = automatic: a guided sequence from the cube shape
+ * and the device's SM count, long chunks first and short ones last (tiles
+ * are handed to the CTAs dynamically).  Results do not depend on it.
+ * AFD_EINVAL if zc < 0. */
 afd_status afd_set_stream_zchunk(afd_ctx *ctx, int zc);
 
 /* Filter a float32 cube in place (Sec. 3.3: n_iter explicit iterations of
@@ -298,7 +301,7 @@ afd_status afd_batch_filter(afd_batch *b, const float *K, const float *spacing, 
  * units), into a HOST array of count floats.  Synchronises the stream. */
 afd_status afd_batch_k(afd_batch *b, float *K_out);
 
-/* Tuning: z planes per tile of the batched streaming kernel (0 = 16).
+/* Tuning: z planes per tile of the batched streaming kernel (0 = 64).
  * Results do not depend on it. */
 afd_status afd_batch_set_zchunk(afd_batch *b, int zc);
 

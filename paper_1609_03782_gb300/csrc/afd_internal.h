@@ -90,10 +90,13 @@ struct BatchDesc {
 };
 
 // roles: null (all descriptors use src_role/dst_role) or per-descriptor
-// (src, dst) pairs in device memory.
+// (src, dst) pairs in device memory.  ctr: null (the list is dealt
+// round-robin) or a tile counter, as for launch_pm_stream.  pdl: launch as a
+// programmatic dependent (only after another pm_step_batch launch).
 cudaError_t launch_pm_batch(int S, int cond, const BatchDesc *desc, const int2 *list,
                             const int2 *roles, int64_t ntiles, int src_role, int dst_role, int grid,
-                            int *err, cudaStream_t stream);
+                            unsigned long long *ctr, unsigned long long base, bool pdl, int *err,
+                            cudaStream_t stream);
 
 // ---- temporally blocked kernel (T iterations per pass, any storage) --------
 struct TbShape {

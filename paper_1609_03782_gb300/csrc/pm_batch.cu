@@ -13,6 +13,7 @@
 // all captured once in a CUDA graph and replayed: one graph launch per call.
 // A cube's result is bit-identical to afd_filter_out on that cube alone with
 // the same K (the per-voxel arithmetic is the same code).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -203,24 +204,40 @@ cudaError_t batch_stats(int S, const BatchDesc *desc, const int64_t *len, int co
     }
 }
 
-// Tiles of every cube for z-chunk zc (0: chosen from the cube's depth), in
-// cube order, x fastest.  Returns the z-chunk used per cube through desc.
+// Tiles of every cube for z-chunk zc (0: 64 planes), in cube order, x
+// fastest, then stably sorted by chunk length, longest first: the tiles are
+// handed out dynamically in this order, so the last ones are the short
+// remainder chunks and the CTAs end close together.  Returns the z-chunk
+// used per cube through desc.
 std::vector<int2> build_tiles(std::vector<BatchDesc> &desc, int zc_req)
 {
     std::vector<int2> list;
+    std::vector<int> len;
     for (size_t c = 0; c < desc.size(); ++c) {
         BatchDesc &d = desc[c];
         d.tiles_x = (d.nx + kStreamTX - 1) / kStreamTX;
         d.tiles_y = (d.ny + kStreamTY - 1) / kStreamTY;
-        int zc = zc_req > 0 ? zc_req : 16;
+        int zc = zc_req > 0 ? zc_req : 64;
         if (zc > d.nz)
             zc = d.nz;
         d.zc = zc;
-        const int nt = d.tiles_x * d.tiles_y * ((d.nz + zc - 1) / zc);
-        for (int t = 0; t < nt; ++t)
+        const int txy = d.tiles_x * d.tiles_y;
+        const int nt = txy * ((d.nz + zc - 1) / zc);
+        for (int t = 0; t < nt; ++t) {
             list.push_back(make_int2(static_cast<int>(c), t));
+            const int z0 = (t / txy) * zc;
+            len.push_back(std::min(zc, d.nz - z0));
+        }
     }
-    return list;
+    std::vector<size_t> order(list.size());
+    for (size_t i = 0; i < order.size(); ++i)
+        order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return len[a] > len[b]; });
+    std::vector<int2> sorted(list.size());
+    for (size_t i = 0; i < order.size(); ++i)
+        sorted[i] = list[order[i]];
+    return sorted;
 }
 
 void free_batch(afd_batch *b)
@@ -269,8 +286,7 @@ afd_status upload_tiles(afd_batch *b)
     const int64_t gmax = static_cast<int64_t>(b->ctx->sm_count) * (b->ctx->stream_bps > 0
                                                                        ? b->ctx->stream_bps
                                                                        : 1);
-    const int64_t rounds = (b->ntiles + gmax - 1) / gmax;
-    b->grid = static_cast<int>((b->ntiles + rounds - 1) / rounds);
+    b->grid = static_cast<int>(b->ntiles < gmax ? b->ntiles : gmax);
     if (b->exec) {  // the tile list is baked into the graph
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
@@ -494,7 +510,10 @@ afd_status afd_batch_filter(afd_batch *b, const float *K, const float *spacing, 
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t le = batch_stats(b->S, b->d_desc,
+            // the passes' tile counter starts from zero at every replay
+            cudaError_t le = cudaMemsetAsync(ctx->d_tiles, 0, sizeof(unsigned long long), b->cap);
+            if (le == cudaSuccess)
+                le = batch_stats(b->S, b->d_desc,
                                          reinterpret_cast<const int64_t *>(
                                              b->d_part + static_cast<size_t>(b->count) * b->bpc * 4),
                                          b->count, b->bpc, b->d_part, b->cap);
@@ -508,7 +527,10 @@ afd_status afd_batch_filter(afd_batch *b, const float *K, const float *spacing, 
                 const int dst = ((n_iter - 1 - i) & 1) ? 2 : 1;
                 const int src = i == 0 ? 0 : (((n_iter - i) & 1) ? 2 : 1);
                 le = afd::launch_pm_batch(b->S, kind, b->d_desc, b->d_list, nullptr, b->ntiles, src, dst,
-                                          b->grid, ctx->d_err, b->cap);
+                                          b->grid, ctx->d_tiles,
+                                          static_cast<unsigned long long>(i) *
+                                              static_cast<unsigned long long>(b->ntiles),
+                                          i > 0, ctx->d_err, b->cap);
             }
             e = cudaStreamEndCapture(b->cap, &graph);
             if (e == cudaSuccess)

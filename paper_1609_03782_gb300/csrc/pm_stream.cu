@@ -246,14 +246,24 @@ struct OneCube {
 
 // Many cubes of a resident batch: per-cube descriptors in global memory and a
 // list of (cube, tile) pairs; `src` and `dst` select the buffers (roles), or
-// per descriptor `roles[c]` = (src, dst) when roles is not null.
+// per descriptor `roles[c]` = (src, dst) when roles is not null.  With a tile
+// counter the list is handed out dynamically as for one cube, else
+// round-robin.
 template <int S>
 struct ManyCubes {
     const BatchDesc *desc;
     const int2 *list;
     const int2 *roles;
     int src, dst;
-    __device__ __forceinline__ int64_t next(int64_t t) const { return t + gridDim.x; }
+    unsigned long long *ctr;
+    unsigned long long base;
+    __device__ __forceinline__ int64_t next(int64_t t) const
+    {
+        if (!ctr)
+            return t + gridDim.x;
+        return static_cast<int64_t>(gridDim.x) +
+               static_cast<int64_t>(atomicAdd(ctr, 1ull) - base);
+    }
     __device__ __forceinline__ void tile(int64_t t, TileInfo<S> &ti) const
     {
         const int2 ct = list[t];
@@ -559,9 +569,10 @@ template <int S, int C>
 __global__ void __maxnreg__(kStreamMaxRegs)
     pm_step_batch(const BatchDesc *__restrict__ desc, const int2 *__restrict__ list,
                   const int2 *__restrict__ roles, int64_t ntiles, int src_role, int dst_role,
-                  int *err)
+                  unsigned long long *ctr, unsigned long long base, int *err)
 {
-    const ManyCubes<S> src{desc, list, roles, src_role, dst_role};
+    grid_dep_launch_dependents();
+    const ManyCubes<S> src{desc, list, roles, src_role, dst_role, ctr, base};
     stream_body<S, C>(src, ntiles, err);
 }
 
@@ -778,45 +789,51 @@ cudaError_t launch_pm_stream_s(int S, int cond, const CUtensorMap &tmap_in, void
 namespace {
 template <int S>
 cudaError_t batch_launch_c(int cond, const BatchDesc *desc, const int2 *list, const int2 *roles,
-                           int64_t ntiles, int src, int dst, int grid, int *err,
-                           cudaStream_t stream)
+                           int64_t ntiles, int src, int dst, int grid, unsigned long long *ctr,
+                           unsigned long long base, bool pdl, int *err, cudaStream_t stream)
 {
-    const size_t smem = pm_stream_smem_bytes();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(kStreamThreads);
+    cfg.dynamicSmemBytes = pm_stream_smem_bytes();
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
     switch (cond) {
     case COND_EXP:
-        pm_step_batch<S, COND_EXP><<<grid, kStreamThreads, smem, stream>>>(desc, list, roles, ntiles,
-                                                                          src, dst, err);
-        break;
+        return cudaLaunchKernelEx(&cfg, pm_step_batch<S, COND_EXP>, desc, list, roles, ntiles, src,
+                                  dst, ctr, base, err);
     case COND_RAT:
-        pm_step_batch<S, COND_RAT><<<grid, kStreamThreads, smem, stream>>>(desc, list, roles, ntiles,
-                                                                          src, dst, err);
-        break;
+        return cudaLaunchKernelEx(&cfg, pm_step_batch<S, COND_RAT>, desc, list, roles, ntiles, src,
+                                  dst, ctr, base, err);
     default:
-        pm_step_batch<S, COND_LIN><<<grid, kStreamThreads, smem, stream>>>(desc, list, roles, ntiles,
-                                                                          src, dst, err);
-        break;
+        return cudaLaunchKernelEx(&cfg, pm_step_batch<S, COND_LIN>, desc, list, roles, ntiles, src,
+                                  dst, ctr, base, err);
     }
-    return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t launch_pm_batch(int S, int cond, const BatchDesc *desc, const int2 *list,
                             const int2 *roles, int64_t ntiles, int src_role, int dst_role, int grid,
-                            int *err, cudaStream_t stream)
+                            unsigned long long *ctr, unsigned long long base, bool pdl, int *err,
+                            cudaStream_t stream)
 {
     switch (S) {
     case STORE_F32:
-        return batch_launch_c<STORE_F32>(cond, desc, list, roles, ntiles, src_role, dst_role, grid, err,
-                                         stream);
+        return batch_launch_c<STORE_F32>(cond, desc, list, roles, ntiles, src_role, dst_role, grid,
+                                         ctr, base, pdl, err, stream);
     case STORE_F16:
-        return batch_launch_c<STORE_F16>(cond, desc, list, roles, ntiles, src_role, dst_role, grid, err,
-                                         stream);
+        return batch_launch_c<STORE_F16>(cond, desc, list, roles, ntiles, src_role, dst_role, grid,
+                                         ctr, base, pdl, err, stream);
     case STORE_BF16:
-        return batch_launch_c<STORE_BF16>(cond, desc, list, roles, ntiles, src_role, dst_role, grid, err,
-                                          stream);
+        return batch_launch_c<STORE_BF16>(cond, desc, list, roles, ntiles, src_role, dst_role, grid,
+                                          ctr, base, pdl, err, stream);
     default:
-        return batch_launch_c<STORE_I16>(cond, desc, list, roles, ntiles, src_role, dst_role, grid, err,
-                                         stream);
+        return batch_launch_c<STORE_I16>(cond, desc, list, roles, ntiles, src_role, dst_role, grid,
+                                         ctr, base, pdl, err, stream);
     }
 }
 

@@ -277,7 +277,7 @@ afd_status launch_round(afd_serve *s, bool *launched)
         const int64_t rounds = (nt + gmax - 1) / gmax;
         const int grid = static_cast<int>((nt + rounds - 1) / rounds);
         e = afd::launch_pm_batch(b->S, k, s->d_desc, s->d_list[p] + seg[k][0], s->d_roles[p], nt,
-                                 0, 1, grid, s->ctx->d_err, st);
+                                 0, 1, grid, nullptr, 0, false, s->ctx->d_err, st);
         s->ctx->launches++;
     }
     if (e == cudaSuccess) {
