@@ -166,10 +166,25 @@ afd_status afd_filter_intensity(afd_ctx *ctx, const float *in, float *out, int64
  * host_out (host_in == host_out is allowed).  Synchronous: returns after the
  * result is in host memory, so the timing of this call includes the
  * host<->device transfers, as the paper's GPU timings do (Sec. 6).  Uses
- * 8*nx*ny*nz bytes of context device memory besides the filter's scratch. */
+ * 8*nx*ny*nz bytes of context device memory (staging slot 0) besides the
+ * filter's scratch. */
 afd_status afd_filter_host(afd_ctx *ctx, const float *host_in, float *host_out, int64_t nx,
                            int64_t ny, int64_t nz, const float *spacing, float K, float dt,
                            int n_iter, afd_conductance cond);
+
+/* afd_filter_host without waiting: enqueues the copy of host_in to the
+ * device (on a context-owned copy stream), the n_iter passes (on the
+ * context's stream) and the copy of the result to host_out (on a second
+ * copy stream), and returns.  Consecutive calls alternate between two
+ * staging slots of 8*nx*ny*nz device bytes each, so one call's copies run
+ * while the previous call's passes do: a sequence of cubes then costs about
+ * max(copies, passes) per cube instead of their sum.  host_in must stay
+ * unchanged and host_out untouched until afd_sync(ctx) returns; page-locked
+ * (pinned) buffers are needed for the overlap (pageable ones work, without
+ * it).  Errors of the asynchronous work are reported by afd_sync. */
+afd_status afd_filter_host_async(afd_ctx *ctx, const float *host_in, float *host_out, int64_t nx,
+                                 int64_t ny, int64_t nz, const float *spacing, float K, float dt,
+                                 int n_iter, afd_conductance cond);
 
 /* Round a float32 cube into a 2-byte storage format (precision line): out[i]
  * = RN(in[i] / scale) in float16 or bfloat16, or RN(in[i] * 1024 / scale)

@@ -48,6 +48,7 @@ def _load():
         "afd_filter": ([vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_out": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_host": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
+        "afd_filter_host_async": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_intensity": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, f32, c_int], c_int),
         "afd_selftest_wait": ([vp, i64], c_int),
         "afd_quantize": ([vp, vp, vp, i64, c_int, f32], c_int),
@@ -234,6 +235,26 @@ def afd_filter_host(ctx: Context, host_in: torch.Tensor, host_out: torch.Tensor,
     _check(_lib.afd_filter_host(ctx.handle, p_in, p_out, nx, ny, nz, _spacing(spacing),
                                 float(K), float(dt), int(n_iter), COND[conductance]),
            "afd_filter_host", ctx)
+    return host_out
+
+
+def afd_filter_host_async(ctx: Context, host_in: torch.Tensor, host_out: torch.Tensor,
+                          K: float, dt: float, n_iter: int, conductance: str = "rational",
+                          spacing=None) -> torch.Tensor:
+    """Enqueue afd_filter_host without waiting (copies on context-owned copy
+    streams, passes on the current stream); host_out is valid after
+    afd_sync.  Pinned tensors let consecutive calls overlap."""
+    for t in (host_in, host_out):
+        if t.dtype != torch.float32 or t.is_cuda:
+            raise ValueError("afd_filter_host_async takes float32 CPU tensors")
+    if host_in.shape != host_out.shape:
+        raise ValueError("input and output shapes differ")
+    p_in, nx, ny, nz = _cube_args(host_in)
+    p_out, _, _, _ = _cube_args(host_out)
+    _use_current_stream(ctx)
+    _check(_lib.afd_filter_host_async(ctx.handle, p_in, p_out, nx, ny, nz, _spacing(spacing),
+                                      float(K), float(dt), int(n_iter), COND[conductance]),
+           "afd_filter_host_async", ctx)
     return host_out
 
 

@@ -443,10 +443,29 @@ afd_status afd_destroy(afd_ctx *ctx)
         return AFD_OK;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    for (int i = 0; i < 2; ++i) {
+        afd_ctx::HostSlot &s = ctx->host_slot[i];
+        if (s.copied_out)
+            cudaEventSynchronize(s.copied_out);
+        if (s.buf)
+            cudaFree(s.buf);
+        if (s.copied_in)
+            cudaEventDestroy(s.copied_in);
+        if (s.filtered)
+            cudaEventDestroy(s.filtered);
+        if (s.copied_out)
+            cudaEventDestroy(s.copied_out);
+    }
+    if (ctx->h2d_stream) {
+        cudaStreamSynchronize(ctx->h2d_stream);
+        cudaStreamDestroy(ctx->h2d_stream);
+    }
+    if (ctx->d2h_stream) {
+        cudaStreamSynchronize(ctx->d2h_stream);
+        cudaStreamDestroy(ctx->d2h_stream);
+    }
     if (ctx->scratch)
         cudaFree(ctx->scratch);
-    if (ctx->stage)
-        cudaFree(ctx->stage);
     if (ctx->lp_scratch)
         cudaFree(ctx->lp_scratch);
     if (ctx->fb_scratch)
@@ -548,32 +567,118 @@ afd_status afd_filter_intensity(afd_ctx *ctx, const float *in, float *out, int64
     return run_passes(ctx, in, out, nx, ny, nz, afd::COND_INT, k, n_iter);
 }
 
+namespace {
+
+// Enqueue one host-to-host filter through staging slot `slot`: the H2D copy
+// on the context's H2D stream, the passes on the context's stream, the D2H
+// copy on its D2H stream, ordered by the slot's events.  A slot's input
+// buffer is refilled only after the passes that read it are done, and its
+// result buffer rewritten only after its copy to the host is done.
+afd_status enqueue_host_filter(afd_ctx *ctx, int slot, const float *host_in, float *host_out,
+                               int64_t nx, int64_t ny, int64_t nz, const float *spacing, float K,
+                               float dt, int n_iter, afd_conductance cond)
+{
+    cudaError_t e = cudaSuccess;
+    if (!ctx->h2d_stream)
+        e = cudaStreamCreateWithFlags(&ctx->h2d_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->d2h_stream)
+        e = cudaStreamCreateWithFlags(&ctx->d2h_stream, cudaStreamNonBlocking);
+    afd_ctx::HostSlot &s = ctx->host_slot[slot];
+    if (e == cudaSuccess && !s.copied_in) {
+        e = cudaEventCreateWithFlags(&s.copied_in, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&s.filtered, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(&s.copied_out, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
+    if (s.bytes < 2 * bytes) {
+        // the slot's old buffer may still be in use: let all its work finish
+        e = cudaEventSynchronize(s.copied_out);
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(s.filtered);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e);
+        if (s.buf)
+            cudaFree(s.buf);
+        s.buf = nullptr;
+        s.bytes = 0;
+        void *p = nullptr;
+        afd_status st = device_alloc(ctx, &p, 2 * bytes);
+        if (st != AFD_OK)
+            return st;
+        s.buf = static_cast<float *>(p);
+        s.bytes = 2 * bytes;
+    }
+    float *d_in = s.buf;
+    float *d_out = s.buf + nx * ny * nz;
+    // (waiting on an event that was never recorded returns at once)
+    e = cudaStreamWaitEvent(ctx->h2d_stream, s.filtered, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_in, host_in, bytes, cudaMemcpyHostToDevice, ctx->h2d_stream);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(s.copied_in, ctx->h2d_stream);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(ctx->stream, s.copied_in, 0);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(ctx->stream, s.copied_out, 0);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    afd_status st = filter_device(ctx, d_in, d_out, nx, ny, nz, spacing, K, dt, n_iter, cond);
+    if (st != AFD_OK)
+        return st;
+    e = cudaEventRecord(s.filtered, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(ctx->d2h_stream, s.filtered, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_out, d_out, bytes, cudaMemcpyDeviceToHost, ctx->d2h_stream);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(s.copied_out, ctx->d2h_stream);
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+}
+
+bool host_args_ok(afd_ctx *ctx, const float *host_in, float *host_out, int64_t nx, int64_t ny,
+                  int64_t nz, const float *spacing, float K, float dt, int n_iter,
+                  afd_conductance cond)
+{
+    return ctx && host_in && host_out && dims_ok(nx, ny, nz) &&
+           params_ok(spacing, K, dt, n_iter, cond);
+}
+
+}  // namespace
+
 afd_status afd_filter_host(afd_ctx *ctx, const float *host_in, float *host_out, int64_t nx,
                            int64_t ny, int64_t nz, const float *spacing, float K, float dt,
                            int n_iter, afd_conductance cond)
 {
-    if (!ctx || !host_in || !host_out || !dims_ok(nx, ny, nz) ||
-        !params_ok(spacing, K, dt, n_iter, cond))
+    if (!host_args_ok(ctx, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter, cond))
         return AFD_EINVAL;
     afd_status st = set_device(ctx);
     if (st != AFD_OK)
         return st;
-    const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
-    st = ensure_buffer(ctx, &ctx->stage, &ctx->stage_bytes, 2 * bytes);
+    st = enqueue_host_filter(ctx, 0, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter, cond);
     if (st != AFD_OK)
         return st;
-    float *d_in = ctx->stage;
-    float *d_out = ctx->stage + nx * ny * nz;
-    cudaError_t e = cudaMemcpyAsync(d_in, host_in, bytes, cudaMemcpyHostToDevice, ctx->stream);
-    if (e != cudaSuccess)
-        return cuda_fail(ctx, e);
-    st = filter_device(ctx, d_in, d_out, nx, ny, nz, spacing, K, dt, n_iter, cond);
-    if (st != AFD_OK)
-        return st;
-    e = cudaMemcpyAsync(host_out, d_out, bytes, cudaMemcpyDeviceToHost, ctx->stream);
-    if (e != cudaSuccess)
-        return cuda_fail(ctx, e);
     return afd_sync(ctx);
+}
+
+afd_status afd_filter_host_async(afd_ctx *ctx, const float *host_in, float *host_out, int64_t nx,
+                                 int64_t ny, int64_t nz, const float *spacing, float K, float dt,
+                                 int n_iter, afd_conductance cond)
+{
+    if (!host_args_ok(ctx, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter, cond))
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    const int slot = static_cast<int>(ctx->host_calls & 1ull);
+    st = enqueue_host_filter(ctx, slot, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter,
+                             cond);
+    if (st == AFD_OK)
+        ctx->host_calls++;
+    return st;
 }
 
 afd_status afd_quantize(afd_ctx *ctx, const float *in, void *out, int64_t n, afd_storage storage,
@@ -815,6 +920,10 @@ afd_status afd_sync(afd_ctx *ctx)
     if (st != AFD_OK)
         return st;
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess && ctx->h2d_stream)
+        e = cudaStreamSynchronize(ctx->h2d_stream);
+    if (e == cudaSuccess && ctx->d2h_stream)
+        e = cudaStreamSynchronize(ctx->d2h_stream);
     if (e == cudaSuccess)
         e = cudaGetLastError();
     if (e != cudaSuccess)

@@ -21,8 +21,18 @@ struct afd_ctx {
     unsigned long long tiles_base = 0;      // counter value at the next launch's start
     float *scratch = nullptr;    // ping-pong partner buffer
     size_t scratch_bytes = 0;
-    float *stage = nullptr;      // device copy for afd_filter_host
-    size_t stage_bytes = 0;
+    // afd_filter_host(_async): two staging slots (device copies of the input
+    // and of the result) so that one call's copies overlap another's passes
+    struct HostSlot {
+        float *buf = nullptr;  // input, then result (2 x the cube)
+        size_t bytes = 0;
+        cudaEvent_t copied_in = nullptr;   // the H2D copy of the input is done
+        cudaEvent_t filtered = nullptr;    // the passes are done
+        cudaEvent_t copied_out = nullptr;  // the D2H copy of the result is done
+    } host_slot[2];
+    unsigned long long host_calls = 0;
+    cudaStream_t h2d_stream = nullptr;  // host -> device copies
+    cudaStream_t d2h_stream = nullptr;  // device -> host copies
     float *lp_scratch = nullptr; // ping-pong partner of afd_filter_ex (any storage)
     size_t lp_scratch_bytes = 0;
     float *fb_scratch = nullptr; // float32 pair for the afd_filter_ex fallback

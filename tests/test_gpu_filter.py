@@ -186,6 +186,31 @@ def test_determinism_and_host_entry(afd, ctx):
     assert np.array_equal(h.numpy().view(np.uint32), a.view(np.uint32))
 
 
+def test_host_async_sequence(afd, ctx):
+    # several cubes in flight through the two staging slots, with different
+    # shapes (a slot grows while the other is busy), parameters and buffer
+    # kinds; each result equals the same filter on the device, bit for bit
+    jobs = [((24, 40, 64), 1.3, 1 / 8, 7, "rational", True),
+            ((16, 33, 96), 0.8, 1 / 16, 4, "exponential", True),
+            ((40, 64, 128), 2.0, 1 / 8, 3, "rational", False),
+            ((24, 40, 64), 1.1, 0.1, 1, "exponential", True),
+            ((9, 20, 36), 1.5, 1 / 8, 5, "rational", False)]
+    hosts, refs = [], []
+    for i, (shape, K, dt, n, cond, pinned) in enumerate(jobs):
+        cube = synth.cutout(shape, 300 + i)
+        refs.append(run(afd, ctx, cube, K, dt, n, cond))
+        h_in = torch.from_numpy(cube.copy())
+        h_out = torch.full(shape, float("nan"))
+        if pinned:
+            h_in, h_out = h_in.pin_memory(), h_out.pin_memory()
+        hosts.append((h_in, h_out))
+    for (h_in, h_out), (shape, K, dt, n, cond, _) in zip(hosts, jobs):
+        afd.afd_filter_host_async(ctx, h_in, h_out, K, dt, n, cond)
+    afd.afd_sync(ctx)
+    for i, ((h_in, h_out), ref) in enumerate(zip(hosts, refs)):
+        assert np.array_equal(h_out.numpy().view(np.uint32), ref.view(np.uint32)), i
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 5])
 def test_out_of_place(afd, ctx, n):
     cube = synth.cube64()[:24].copy()
