@@ -447,25 +447,22 @@ def run_afd(args):
     ctx = afd.afd_create(local)
     stream = torch.cuda.current_stream(dev)
 
-    filt_events = []
 
-    def step(record):
-        sig = afd.afd_noise_rms(ctx, d_in)                        # a1
-        if record:
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        afd.afd_filter_out(ctx, d_in, d_out, K_SIGMA * sig, DT, N_ITER, COND)  # a3-a6
-        if record:
-            e1.record(stream)
-            filt_events.append((e0, e1))
-        afd.afd_stats(ctx, d_out, out4)                           # a8
-        return sig
+    K_dev = torch.zeros(1, dtype=torch.float32, device=dev)
+
+    def step():
+        # a1 noise rms, a2 K = 1.0 rms and the coefficients (on the device),
+        # a3-a6 the 50 passes; then a8 the statistics of the result
+        afd.afd_filter_rel(ctx, d_in, d_out, K_SIGMA, DT, N_ITER, COND, K_out=K_dev)
+        afd.afd_stats(ctx, d_out, out4)
 
     for _ in range(max(args.warmup, 0)):
-        sig = step(False)
+        step()
     torch.cuda.synchronize(dev)
     afd.afd_sync(ctx)
+    sig = float(K_dev.item()) / K_SIGMA
+    afd.afd_pass_timing_read(ctx)          # clear
+    afd.afd_pass_timing(ctx, True)         # events around each call's passes
 
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -481,7 +478,7 @@ def run_afd(args):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
-        sig = step(True)
+        step()
     t1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
@@ -489,8 +486,10 @@ def run_afd(args):
     afd.afd_sync(ctx)
     launches = afd.afd_launch_count(ctx) - launches0
     ms = max_over_ranks(t0.elapsed_time(t1))
-    filt_ms = sum(a.elapsed_time(b) for a, b in filt_events)
-    launch_ms = max_over_ranks(filt_ms / (args.steps * N_ITER))
+    afd.afd_pass_timing(ctx, False)
+    filt_ms, filt_passes = afd.afd_pass_timing_read(ctx)
+    assert filt_passes == args.steps * N_ITER, filt_passes
+    launch_ms = max_over_ranks(filt_ms / filt_passes)
 
     # conservation of the last step's result (FP64 sums of the FP32 fields)
     s_in = afd.afd_sum(ctx, d_in)
@@ -557,11 +556,15 @@ def run_afd(args):
                        "parallelism": "one independent cube per GPU" if world > 1 else "1 GPU",
                        "l2": "inputs larger than L2 (268 MB cube in + 268 MB out + 268 MB "
                              "ping-pong scratch vs 129 MB L2); no flush",
-                       "step": "a1 noise rms -> K, 50 filter iterations out of place, a8 FP64 "
-                               "sum of the result"},
+                       "step": "afd_filter_rel: a1 noise rms, a2 K = 1.0 rms and coefficients "
+                               "on the device, 50 filter iterations out of place; then a8 "
+                               "statistics of the result (no host round trip in the step)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "kernel": "pm_step_stream (one iteration per launch)",
+                         "timing": "CUDA events recorded by the library on its stream around "
+                                   "each call's 50 passes (afd_pass_timing), summed over the "
+                                   "timed steps",
                          "bytes_per_launch": bytes_per_launch,
                          "launch_ms": launch_ms, "traffic": profiled_traffic()},
             "cpu_baseline": cpu,

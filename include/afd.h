@@ -141,6 +141,21 @@ afd_status afd_filter_out(afd_ctx *ctx, const float *in, float *out, int64_t nx,
                           int64_t nz, const float *spacing, float K, float dt, int n_iter,
                           afd_conductance cond);
 
+/* afd_filter_out with K given in units of the input's noise level (Sec. 3.3
+ * states K relative to the rms of the noise): K = k_rms x rms, rms the rms
+ * of the negative voxels of `in` (as afd_noise_rms computes it), rounded to
+ * float.  On the streaming kernel (nx % 4 == 0, 16-byte aligned cubes, kernel
+ * not forced to SIMPLE) the statistics, K and the coefficients are computed
+ * on the device and the call returns without waiting; otherwise the rms
+ * takes a round trip through the host.  Either way the result is bit for bit
+ * afd_filter_out's with that K.  K_out: DEVICE float receiving K (may be
+ * NULL).  An input without negative voxels has rms 0: K = 0 and the result
+ * equals the input.  AFD_EINVAL if k_rms is not finite and > 0, or as
+ * afd_filter_out. */
+afd_status afd_filter_rel(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
+                          int64_t nz, const float *spacing, float k_rms, float dt, int n_iter,
+                          afd_conductance cond, float *K_out);
+
 /* The paper's own intensity-driven gradient filter (Sec. 3.3, the explicit
  * update after eq. "conductivepara"), out of place:
  *     I' = I + tau (C_x D_x + C_y D_y + C_z D_z) / (1 + I^2 / (K^2 rms^2))
@@ -257,6 +272,15 @@ afd_status afd_sum(afd_ctx *ctx, const float *cube, int64_t n, double *out);
  * AFD_ECUDA for a CUDA error, AFD_ETIMEOUT when a kernel's bounded wait
  * expired (the error word is then cleared). */
 afd_status afd_sync(afd_ctx *ctx);
+
+/* Pass timing, for profiling: while on, every float32 filter call that runs
+ * on the streaming kernel records a pair of CUDA events on the context's
+ * stream around its sequence of passes (after the statistics of
+ * afd_filter_rel, before any copy).  afd_pass_timing_read waits for the
+ * last recorded event, returns the summed device time of the recorded
+ * sequences (ms) and their number of passes, and clears the record. */
+afd_status afd_pass_timing(afd_ctx *ctx, int on);
+afd_status afd_pass_timing_read(afd_ctx *ctx, double *ms, int64_t *passes);
 
 /* Diagnostic of the bounded-wait machinery: launches one kernel whose
  * mbarrier wait can never complete and gives up after limit_ns nanoseconds

@@ -49,6 +49,10 @@ def _load():
         "afd_filter_out": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_host": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_host_async": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
+        "afd_filter_rel": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int, vp], c_int),
+        "afd_pass_timing": ([vp, c_int], c_int),
+        "afd_pass_timing_read": ([vp, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_int64)], c_int),
         "afd_filter_intensity": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, f32, c_int], c_int),
         "afd_selftest_wait": ([vp, i64], c_int),
         "afd_quantize": ([vp, vp, vp, i64, c_int, f32], c_int),
@@ -236,6 +240,41 @@ def afd_filter_host(ctx: Context, host_in: torch.Tensor, host_out: torch.Tensor,
                                 float(K), float(dt), int(n_iter), COND[conductance]),
            "afd_filter_host", ctx)
     return host_out
+
+
+def afd_filter_rel(ctx: Context, cube_in: torch.Tensor, cube_out: torch.Tensor, k_rms: float,
+                   dt: float, n_iter: int, conductance: str = "rational", spacing=None,
+                   K_out: torch.Tensor | None = None) -> torch.Tensor:
+    """afd_filter_out with K = k_rms x (noise rms of cube_in), computed on the
+    device; K_out (a CUDA float32 tensor of one element) receives K."""
+    p_in, nx, ny, nz = _cube_args(cube_in)
+    p_out, _, _, _ = _cube_args(cube_out)
+    if cube_in.shape != cube_out.shape or cube_in.dtype != torch.float32 or \
+            cube_out.dtype != torch.float32:
+        raise ValueError("float32 cubes of one shape expected")
+    kp = None
+    if K_out is not None:
+        if not K_out.is_cuda or K_out.dtype != torch.float32 or K_out.numel() < 1:
+            raise ValueError("K_out must be a CUDA float32 tensor")
+        kp = ctypes.c_void_p(K_out.data_ptr())
+    _use_current_stream(ctx, cube_in)
+    _check(_lib.afd_filter_rel(ctx.handle, p_in, p_out, nx, ny, nz, _spacing(spacing),
+                               float(k_rms), float(dt), int(n_iter), COND[conductance], kp),
+           "afd_filter_rel", ctx)
+    return cube_out
+
+
+def afd_pass_timing(ctx: Context, on: bool) -> None:
+    _check(_lib.afd_pass_timing(ctx.handle, 1 if on else 0), "afd_pass_timing", ctx)
+
+
+def afd_pass_timing_read(ctx: Context):
+    """(summed device ms, passes) of the pass sequences recorded since the last read."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(_lib.afd_pass_timing_read(ctx.handle, ctypes.byref(ms), ctypes.byref(n)),
+           "afd_pass_timing_read", ctx)
+    return ms.value, n.value
 
 
 def afd_filter_host_async(ctx: Context, host_in: torch.Tensor, host_out: torch.Tensor,

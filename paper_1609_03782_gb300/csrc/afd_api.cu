@@ -164,6 +164,29 @@ afd_status set_device(afd_ctx *ctx)
     return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
 }
 
+// Pass timing: record a begin event now and hand back the end event to be
+// recorded after the passes.
+cudaError_t timing_begin(afd_ctx *ctx, cudaEvent_t *end)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&b);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(a, ctx->stream);
+    if (e != cudaSuccess) {
+        if (a)
+            cudaEventDestroy(a);
+        if (b)
+            cudaEventDestroy(b);
+        return e;
+    }
+    ctx->tev.push_back(a);
+    ctx->tev.push_back(b);
+    *end = b;
+    return cudaSuccess;
+}
+
 // Zero the streaming kernel's tile counter (stream-ordered) before a sequence
 // of launches.
 cudaError_t tiles_reset(afd_ctx *ctx)
@@ -178,7 +201,8 @@ cudaError_t tiles_reset(afd_ctx *ctx)
 // between `out` and scratch so that the last pass lands in `out`; in place
 // they alternate starting with scratch, and an odd count ends with a copy.
 afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
-                      int64_t nz, int kind, const afd::Coef &k, int n_iter);
+                      int64_t nz, int kind, const afd::Coef &k, int n_iter,
+                      const afd::Coef *kdev = nullptr);
 
 afd_status filter_device(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
                          int64_t nz, const float *spacing, float K, float dt, int n_iter,
@@ -196,9 +220,11 @@ afd_status filter_device(afd_ctx *ctx, const float *in, float *out, int64_t nx, 
     return run_passes(ctx, in, out, nx, ny, nz, kind, k, n_iter);
 }
 
-// n_iter >= 1 passes of conductance kind `kind` with coefficients k.
+// n_iter >= 1 passes of conductance kind `kind` with coefficients k, or
+// with the coefficients at kdev (device memory; streaming kernel only).
 afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
-                      int64_t nz, int kind, const afd::Coef &k, int n_iter)
+                      int64_t nz, int kind, const afd::Coef &k, int n_iter,
+                      const afd::Coef *kdev)
 {
     const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
     cudaError_t e = cudaSuccess;
@@ -224,6 +250,8 @@ afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int
     } else if (ctx->kernel == AFD_KERNEL_AUTO) {
         use_stream = fits;
     }
+    if (kdev && !use_stream)
+        return AFD_EINVAL;  // callers check this first
 
     if (use_stream) {
         if (ctx->stream_bps == 0) {
@@ -248,16 +276,24 @@ afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int
             afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny), static_cast<int>(nz),
                                 ctx->sm_count, ctx->stream_bps, ctx->zc_hint);
         e = tiles_reset(ctx);
+        cudaEvent_t tend = nullptr;
+        if (e == cudaSuccess && ctx->timing)
+            e = timing_begin(ctx, &tend);
         for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
             const float *src = src_of(i);
             const int m = (src == in) ? 0 : (src == out ? 1 : 2);
             afd::StreamPlan pl = plan;
             pl.pdl = i > 0;
+            pl.kdev = kdev;
             e = afd::launch_pm_stream(kind, maps[m], dst_of(i), static_cast<int>(nx),
                                       static_cast<int>(ny), static_cast<int>(nz), k, pl,
                                       ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream);
             ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
             ctx->launches++;
+        }
+        if (e == cudaSuccess && tend) {
+            e = cudaEventRecord(tend, ctx->stream);
+            ctx->timed_passes += n_iter;
         }
     } else {
         for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
@@ -413,7 +449,8 @@ afd_status afd_create(afd_ctx **out, int device, void *cuda_stream)
     }
     ctx->part_blocks = ctx->sm_count * 4;
     const size_t small = sizeof(int) * 32 + sizeof(double) * 4 +
-                         sizeof(double) * 4 * static_cast<size_t>(ctx->part_blocks);
+                         sizeof(double) * 4 * static_cast<size_t>(ctx->part_blocks) +
+                         sizeof(afd::Coef);
     void *p = nullptr;
     afd_status st = device_alloc(ctx, &p, small);
     if (st != AFD_OK) {
@@ -424,6 +461,7 @@ afd_status afd_create(afd_ctx **out, int device, void *cuda_stream)
     ctx->d_tiles = reinterpret_cast<unsigned long long *>(ctx->d_err + 16);
     ctx->d_out4 = reinterpret_cast<double *>(static_cast<char *>(p) + sizeof(int) * 32);
     ctx->d_part = ctx->d_out4 + 4;
+    ctx->d_coef = reinterpret_cast<afd::Coef *>(ctx->d_part + 4 * ctx->part_blocks);
     e = cudaMemset(ctx->d_err, 0, sizeof(int) * 32);
     if (e == cudaSuccess)
         e = cudaMallocHost(reinterpret_cast<void **>(&ctx->h_out4), 4 * sizeof(double));
@@ -470,6 +508,8 @@ afd_status afd_destroy(afd_ctx *ctx)
         cudaFree(ctx->lp_scratch);
     if (ctx->fb_scratch)
         cudaFree(ctx->fb_scratch);
+    for (cudaEvent_t ev : ctx->tev)
+        cudaEventDestroy(ev);
     if (ctx->d_err)
         cudaFree(ctx->d_err);
     if (ctx->h_out4)
@@ -532,6 +572,57 @@ afd_status afd_filter_out(afd_ctx *ctx, const float *in, float *out, int64_t nx,
     if (st != AFD_OK)
         return st;
     return filter_device(ctx, in, out, nx, ny, nz, spacing, K, dt, n_iter, cond);
+}
+
+afd_status afd_filter_rel(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
+                          int64_t nz, const float *spacing, float k_rms, float dt, int n_iter,
+                          afd_conductance cond, float *K_out)
+{
+    if (!ctx || !in || !out || !dims_ok(nx, ny, nz) || !(k_rms > 0.0f) || !std::isfinite(k_rms) ||
+        !params_ok(spacing, 1.0f, dt, n_iter, cond))
+        return AFD_EINVAL;
+    const int64_t n = nx * ny * nz;
+    if (in != out) {
+        const size_t bytes = static_cast<size_t>(n) * sizeof(float);
+        const char *a = reinterpret_cast<const char *>(in);
+        const char *b = reinterpret_cast<const char *>(out);
+        if (a < b + bytes && b < a + bytes)
+            return AFD_EINVAL;
+    }
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    const bool on_device = ctx->kernel != AFD_KERNEL_SIMPLE && n_iter > 0 &&
+                           stream_kernel_fits(in, out, nx);
+    if (!on_device) {
+        // through the host: the same rms, K and host coefficients
+        double rms = 0.0;
+        st = afd_noise_rms(ctx, in, n, &rms);
+        if (st != AFD_OK)
+            return st;
+        const float K = static_cast<float>(static_cast<double>(k_rms) * rms);
+        if (K_out) {
+            cudaError_t e = cudaMemcpy(K_out, &K, sizeof(float), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e);
+        }
+        return filter_device(ctx, in, out, nx, ny, nz, spacing, K, dt, n_iter, cond);
+    }
+    st = stats_device(ctx, in, n, ctx->d_out4);
+    if (st != AFD_OK)
+        return st;
+    int kind = 0;
+    // B terms (independent of K) and the kind from the host formulas
+    const afd::Coef b = afd::make_coef(spacing, 1.0f, dt, cond == AFD_COND_EXPONENTIAL, &kind);
+    const double h[3] = {spacing ? spacing[0] : 1.0, spacing ? spacing[1] : 1.0,
+                         spacing ? spacing[2] : 1.0};
+    cudaError_t e = afd::launch_rel_coef(ctx->d_out4, static_cast<double>(k_rms), kind,
+                                         static_cast<double>(dt), h, b, ctx->d_coef, K_out,
+                                         ctx->stream);
+    ctx->launches++;
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    return run_passes(ctx, in, out, nx, ny, nz, kind, b, n_iter, ctx->d_coef);
 }
 
 afd_status afd_filter_intensity(afd_ctx *ctx, const float *in, float *out, int64_t nx,
@@ -939,6 +1030,40 @@ afd_status afd_sync(afd_ctx *ctx)
         return AFD_ETIMEOUT;
     }
     return AFD_OK;
+}
+
+afd_status afd_pass_timing(afd_ctx *ctx, int on)
+{
+    if (!ctx)
+        return AFD_EINVAL;
+    ctx->timing = on != 0;
+    return AFD_OK;
+}
+
+afd_status afd_pass_timing_read(afd_ctx *ctx, double *ms, int64_t *passes)
+{
+    if (!ctx || !ms || !passes)
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    double total = 0.0;
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i + 1 < ctx->tev.size(); i += 2) {
+        float t = 0.0f;
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(ctx->tev[i + 1]);
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&t, ctx->tev[i], ctx->tev[i + 1]);
+        total += static_cast<double>(t);
+    }
+    for (cudaEvent_t ev : ctx->tev)
+        cudaEventDestroy(ev);
+    ctx->tev.clear();
+    *ms = total;
+    *passes = ctx->timed_passes;
+    ctx->timed_passes = 0;
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
 }
 
 afd_status afd_selftest_wait(afd_ctx *ctx, int64_t limit_ns)

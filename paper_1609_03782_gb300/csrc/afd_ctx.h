@@ -4,10 +4,12 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/afd.h"
+#include "afd_math.cuh"
 
 struct afd_ctx {
     int device = 0;
@@ -41,8 +43,13 @@ struct afd_ctx {
     double *d_part = nullptr;    // stats partials
     int part_blocks = 0;
     double *d_out4 = nullptr;    // stats result (device)
+    afd::Coef *d_coef = nullptr; // coefficients computed on the device (afd_filter_rel)
     double *h_out4 = nullptr;    // stats result (pinned host)
     uint64_t launches = 0;
+    // pass timing (afd_pass_timing): event pairs around each pass sequence
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;  // begin, end, begin, end, ...
+    int64_t timed_passes = 0;
     char errstr[256] = {0};
 };
 

@@ -54,6 +54,8 @@ struct StreamPlan {
     // (only when that kernel is a streaming pass: its CTAs then overlap that
     // pass's last tiles)
     bool pdl;
+    // coefficients in device memory (null: the Coef argument of the launch)
+    const Coef *kdev;
 };
 
 // Tiles are handed out through a 64-bit counter in device memory: zero it
@@ -144,6 +146,12 @@ cudaError_t launch_dequantize(int S, const void *in, float *out, int64_t n, floa
 // ---- FP64 statistics -------------------------------------------------------
 constexpr int kStatsThreads = 256;
 // partials: 4 doubles per block; out4: sum, sum sq, negative sum sq, count
+// Noise-relative coefficients: from launch_stats' out4, K = k_rms x rms
+// (rms of the negative voxels) and the coefficients of conductance `kind`
+// into *coef (device); A on the device, the B terms taken from b (host
+// make_coef).  K_out (device, may be null) receives K.
+cudaError_t launch_rel_coef(const double *out4, double k_rms, int kind, double dt, const double h[3],
+                            const Coef &b, Coef *coef, float *K_out, cudaStream_t stream);
 cudaError_t launch_stats(const float *x, int64_t n, double *partials, int nblocks, double *out4,
                          cudaStream_t stream);
 

@@ -130,6 +130,24 @@ inline Coef make_coef_intensity(const float *C, float K, float rms, float tau)
     return c;
 }
 
+// Device: the A coefficient of one axis, with make_coef's operations (double
+// precision, rounded once to float by the caller), for K given on the device
+// (noise-relative K).  The spacing-only B terms involve log2 and come from
+// the host's make_coef, so both sides produce the same floats.
+__device__ inline double coef_a_device(double Kd, int kind, double dt, double h)
+{
+    const double fmax = 3.4028234663852886e38;
+    if (kind == COND_LIN)
+        return dt / (h * h);
+    if (kind == COND_EXP) {
+        const double kh = Kd * h;
+        const double v = -1.4426950408889634074 / (kh * kh);
+        return (v >= -fmax) ? v : -fmax;
+    }
+    const double v = 1.0 / (Kd * Kd * dt);
+    return (v <= fmax) ? v : fmax;
+}
+
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float r;

@@ -153,29 +153,10 @@ __global__ void batch_coef_kernel(BatchDesc *__restrict__ desc, int count, int b
     kout[c] = K;
     // coefficients in storage units: K_s = K * units (exact, units = 2^m)
     const double Kd = static_cast<double>(K) / inv_units;
-    const double fmax = 3.4028234663852886e38;
-    const double h[3] = {h0, h1, h2};
-    float A[3];
-    for (int a = 0; a < 3; ++a) {
-        double v;
-        if (kind == COND_LIN) {
-            v = dt / (h[a] * h[a]);
-        } else if (kind == COND_EXP) {
-            const double kh = Kd * h[a];
-            v = -1.4426950408889634074 / (kh * kh);
-            if (!(v >= -fmax))
-                v = -fmax;
-        } else {
-            v = 1.0 / (Kd * Kd * dt);
-            if (!(v <= fmax))
-                v = fmax;
-        }
-        A[a] = static_cast<float>(v);
-    }
     Coef k;
-    k.ax = A[0];
-    k.ay = A[1];
-    k.az = A[2];
+    k.ax = static_cast<float>(coef_a_device(Kd, kind, dt, h0));
+    k.ay = static_cast<float>(coef_a_device(Kd, kind, dt, h1));
+    k.az = static_cast<float>(coef_a_device(Kd, kind, dt, h2));
     k.bx = b0;
     k.by = b1;
     k.bz = b2;

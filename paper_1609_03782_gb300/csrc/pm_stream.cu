@@ -220,6 +220,7 @@ struct OneCube {
     unsigned long long *ctr;
     unsigned long long base;
     Coef k;
+    const Coef *kdev;  // if set: the coefficients, in device memory (written by an earlier kernel)
     __device__ __forceinline__ void tile(int t, TileInfo<S> &ti) const
     {
         const TileCoord tc = decode_tile(t, tiles_x, txy, *lv, nz);
@@ -235,7 +236,7 @@ struct OneCube {
         ti.px = nx;
         ti.map = map;
         ti.out = out;
-        ti.k = k;
+        ti.k = kdev ? *kdev : k;
     }
     __device__ __forceinline__ int64_t next(int64_t) const
     {
@@ -558,10 +559,11 @@ template <int S, int C>
 __global__ void __maxnreg__(kStreamMaxRegs)
     pm_step_stream(const __grid_constant__ CUtensorMap tmap, typename Store<S>::T *__restrict__ out,
                    int nx, int ny, int nz, int tiles_x, int txy, const __grid_constant__ ZLevels lv,
-                   int ntiles, unsigned long long *ctr, unsigned long long base, Coef kc, int *err)
+                   int ntiles, unsigned long long *ctr, unsigned long long base, Coef kc,
+                   const Coef *kdev, int *err)
 {
     grid_dep_launch_dependents();  // the next pass may take SMs as this one frees them
-    const OneCube<S> src{&tmap, out, nx, ny, nz, tiles_x, txy, &lv, ctr, base, kc};
+    const OneCube<S> src{&tmap, out, nx, ny, nz, tiles_x, txy, &lv, ctr, base, kc, kdev};
     stream_body<S, C>(src, ntiles, err);
 }
 
@@ -718,6 +720,7 @@ StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_s
     p.ntiles = txy * p.tiles_z;
     p.grid = static_cast<int>(p.ntiles < gmax ? p.ntiles : gmax);
     p.pdl = false;
+    p.kdev = nullptr;
     return p;
 }
 
@@ -742,7 +745,7 @@ cudaError_t stream_launch(const CUtensorMap &tmap, void *out, int nx, int ny, in
     return cudaLaunchKernelEx(&cfg, pm_step_stream<S, C>, tmap,
                               static_cast<typename Store<S>::T *>(out), nx, ny, nz, plan.tiles_x,
                               plan.tiles_x * plan.tiles_y, plan.lv, static_cast<int>(plan.ntiles),
-                              ctr, base, k, err);
+                              ctr, base, k, plan.kdev, err);
 }
 template <int S>
 cudaError_t stream_launch_c(int cond, const CUtensorMap &tmap, void *out, int nx, int ny, int nz,

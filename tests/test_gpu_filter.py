@@ -186,6 +186,39 @@ def test_determinism_and_host_entry(afd, ctx):
     assert np.array_equal(h.numpy().view(np.uint32), a.view(np.uint32))
 
 
+@pytest.mark.parametrize("shape,cond,k,n", [((24, 40, 64), "rational", 1.0, 7),
+                                             ((16, 33, 96), "exponential", 1.5, 4),
+                                             ((10, 12, 30), "rational", 2.0, 3)])  # nx % 4 != 0
+def test_filter_rel_equals_host_K(afd, ctx, shape, cond, k, n):
+    # K relative to the noise rms, computed on the device: the same K and the
+    # same result, bit for bit, as afd_filter_out with K from afd_noise_rms
+    cube = synth.cutout(shape, 400 + n)
+    src = torch.from_numpy(cube).cuda()
+    sig = afd.afd_noise_rms(ctx, src)
+    K = float(np.float32(np.float32(k) * sig))
+    ref = torch.empty_like(src)
+    afd.afd_filter_out(ctx, src, ref, K, 1 / 8, n, cond, (1.0, 1.25, 0.8))
+    got = torch.full_like(src, float("nan"))
+    K_dev = torch.zeros(1, dtype=torch.float32, device="cuda")
+    afd.afd_filter_rel(ctx, src, got, k, 1 / 8, n, cond, (1.0, 1.25, 0.8), K_out=K_dev)
+    afd.afd_sync(ctx)
+    assert float(K_dev.item()) == K
+    assert torch.equal(got.view(torch.int32), ref.view(torch.int32))
+
+
+def test_filter_rel_without_noise_is_identity(afd, ctx):
+    cube = np.abs(synth.cutout((8, 16, 32), 7)) + 1.0      # no negative voxel: rms 0
+    src = torch.from_numpy(cube).cuda()
+    got = torch.empty_like(src)
+    K_dev = torch.full((1,), -1.0, device="cuda")
+    afd.afd_filter_rel(ctx, src, got, 1.5, 1 / 8, 5, "rational", K_out=K_dev)
+    afd.afd_sync(ctx)
+    assert float(K_dev.item()) == 0.0
+    assert torch.equal(got, src)
+    with pytest.raises(afd.AfdError):
+        afd.afd_filter_rel(ctx, src, got, 0.0, 1 / 8, 5, "rational")
+
+
 def test_host_async_sequence(afd, ctx):
     # several cubes in flight through the two staging slots, with different
     # shapes (a slot grows while the other is busy), parameters and buffer
