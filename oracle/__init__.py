@@ -23,6 +23,8 @@ intensity_filter     the paper's intensity-driven update (Sec. 3.3, eq. after
 stats / noise_rms    FP64 sums and the negative-half noise estimate (K is set
                      in units of the noise level, Sec. 3.3)
 quantize/dequantize  2-byte storage formats with a power-of-two per-cube scale
+f_diagnostic         the smoothing-quality parameter F with its error sigma_F
+                     (Sec. 4) and the recovered-signal fraction F_M (Sec. 5)
 """
 from __future__ import annotations
 
@@ -70,6 +72,8 @@ def load_library(path: str):
                                          dbl, dbl, dbl, dbl, c_int]
     lib.orc_intensity_filter.restype = c_int
     lib.orc_stats.argtypes = [vp, i64, vp]
+    lib.orc_fdiag.argtypes = [vp, vp, vp, i64, i64, i64, vp, dbl, dbl, vp]
+    lib.orc_fdiag.restype = ctypes.c_int
     lib.orc_stats.restype = None
     return lib
 
@@ -165,6 +169,50 @@ def noise_rms(cube) -> float:
     """
     s = stats(cube)
     return math.sqrt(s["negsumsq"] / s["nneg"]) if s["nneg"] else 0.0
+
+
+def f_diagnostic(orig, filt, model=None, roi=None, rms_o=None, rms_f=None, nsig=3.0,
+                 beam=1.0, lib=None) -> dict:
+    """The paper's smoothing-quality diagnostic over a ROI box.
+
+    F = |S_of| / |S_oo| (Sec. 4, eqs. "F_equa" and "Sequa"), with masks
+    M_i = [I_i >= nsig * rms_i] (eq. "Mfequa", nsig = 3 in the paper) and the
+    sums taken over the ORIGINAL intensities.  sigma_F propagates
+    sigma_S_oi = sqrt(N_i) rms_i (Sec. 4), with N_i the number of independent
+    voxels in mask i: the mask's voxel count divided by `beam`, the number of
+    voxels per independent element (1 for uncorrelated noise).  With the
+    noiseless model, F_M = |S_mf| / |S_m| (Sec. 5, eq. "sums_equa").
+    rms_o / rms_f default to noise_rms of the full cubes (the paper assumes
+    the rms constant over the cube).  roi = (x0, x1, y0, y1, z0, z1), None for
+    the whole cube.
+    """
+    Io = np.ascontiguousarray(orig, dtype=np.float32)
+    If = np.ascontiguousarray(filt, dtype=np.float32)
+    if Io.shape != If.shape or Io.ndim != 3:
+        raise ValueError("original and filtered cubes must be 3-D of one shape")
+    nz, ny, nx = Io.shape
+    Im = None if model is None else np.ascontiguousarray(model, dtype=np.float32)
+    if Im is not None and Im.shape != Io.shape:
+        raise ValueError("model cube shape differs")
+    box = np.array(roi if roi is not None else (0, nx, 0, ny, 0, nz), dtype=np.int64)
+    ro = noise_rms(Io) if rms_o is None else float(rms_o)
+    rf = noise_rms(If) if rms_f is None else float(rms_f)
+    out = np.zeros(6, dtype=np.float64)
+    rc = (lib or _load()).orc_fdiag(Io.ctypes.data, If.ctypes.data,
+                           None if Im is None else Im.ctypes.data, nx, ny, nz,
+                           box.ctypes.data, nsig * ro, nsig * rf, out.ctypes.data)
+    if rc != 0:
+        raise ValueError("empty or out-of-range ROI")
+    s_of, s_oo, s_mf, s_m, n_o, n_f = (float(v) for v in out)
+    r = {"S_of": s_of, "S_oo": s_oo, "S_mf": s_mf, "S_m": s_m, "N_o": int(n_o),
+         "N_f": int(n_f), "rms_o": ro, "rms_f": rf}
+    r["F"] = abs(s_of) / abs(s_oo) if s_oo != 0.0 else math.nan
+    sig_of = math.sqrt(n_f / beam) * rf
+    sig_oo = math.sqrt(n_o / beam) * ro
+    r["sigma_F"] = (math.sqrt(sig_of ** 2 / s_oo ** 2 + s_of ** 2 * sig_oo ** 2 / s_oo ** 4)
+                    if s_oo != 0.0 else math.nan)
+    r["F_M"] = (abs(s_mf) / abs(s_m) if (Im is not None and s_m != 0.0) else math.nan)
+    return r
 
 
 # --------------------------------------------------------------------------

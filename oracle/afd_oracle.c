@@ -187,3 +187,56 @@ void orc_stats(const float *I, int64_t n, double out[4])
     out[2] = ns2;
     out[3] = nneg;
 }
+
+/*
+ * Smoothing-quality sums of Sec. 4 (eqs. "F_equa", "Sequa", "Mfequa") and of
+ * the recovered-signal fraction of Sec. 5 (eq. "sums_equa"), over the ROI
+ * box [roi[0], roi[1]) x [roi[2], roi[3]) x [roi[4], roi[5]) (x, y, z).
+ *
+ * The masks are M_o = [I_o >= t_o] and M_f = [I_f >= t_f], where t_i is a
+ * multiple (3 in the paper) of cube i's rms.  The sums always take the
+ * ORIGINAL cube's intensities, as Sec. 4 stresses.  Im, the noiseless model,
+ * may be NULL.
+ *   out[0] = S_of = sum I_o M_f       out[1] = S_oo = sum I_o M_o
+ *   out[2] = S_mf = sum I_m M_f       out[3] = S_m  = sum I_m
+ *   out[4] = N_o  = sum M_o           out[5] = N_f  = sum M_f
+ * Returns -1 for an empty or out-of-range box.
+ */
+int orc_fdiag(const float *Io, const float *If, const float *Im, int64_t nx, int64_t ny,
+              int64_t nz, const int64_t roi[6], double t_o, double t_f, double out[6])
+{
+    if (roi[0] < 0 || roi[1] > nx || roi[0] >= roi[1] || roi[2] < 0 || roi[3] > ny ||
+        roi[2] >= roi[3] || roi[4] < 0 || roi[5] > nz || roi[4] >= roi[5])
+        return -1;
+    double s_of = 0.0, s_oo = 0.0, s_mf = 0.0, s_m = 0.0, n_o = 0.0, n_f = 0.0;
+    for (int64_t z = roi[4]; z < roi[5]; ++z)
+        for (int64_t y = roi[2]; y < roi[3]; ++y)
+            for (int64_t x = roi[0]; x < roi[1]; ++x) {
+                const int64_t p = x + nx * (y + ny * z);
+                const double io = (double)Io[p];
+                const double iff = (double)If[p];
+                const int mo = io >= t_o;
+                const int mf = iff >= t_f;
+                if (mo) {
+                    s_oo += io;
+                    n_o += 1.0;
+                }
+                if (mf) {
+                    s_of += io;
+                    n_f += 1.0;
+                }
+                if (Im) {
+                    const double im = (double)Im[p];
+                    s_m += im;
+                    if (mf)
+                        s_mf += im;
+                }
+            }
+    out[0] = s_of;
+    out[1] = s_oo;
+    out[2] = s_mf;
+    out[3] = s_m;
+    out[4] = n_o;
+    out[5] = n_f;
+    return 0;
+}

@@ -3,7 +3,9 @@
 Each mutant below is a copy of ``oracle/afd_oracle.c`` with one typical slip
 planted (a dropped axis, a flipped difference, a wrong conductance, a missing
 spacing factor, an in-place Gauss-Seidel sweep, an extra iteration, a
-Dirichlet instead of a zero-flux boundary, a wrong stride, a wrong exponent).
+Dirichlet instead of a zero-flux boundary, a wrong stride, a wrong exponent;
+for the F diagnostic a strict mask threshold, the filtered intensities in
+S_of, and the original mask in place of the filtered one).
 It is compiled on the CPU into a temporary library and run through the same
 pins as ``test_oracle_pins.py``; at least one pin must fail for every mutant.
 """
@@ -16,7 +18,7 @@ import numpy as np
 import pytest
 
 import oracle
-from test_oracle_pins import frac_pm_facewise, heat_closed_form, impulse
+from test_oracle_pins import fdiag_hand_cubes, frac_pm_facewise, heat_closed_form, impulse
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "afd_oracle.c")
 
@@ -39,6 +41,11 @@ MUTANTS = {
     "wrong_y_stride": ("const int64_t stride[3] = {1, nx, nx * ny};\n    double *cur = I, *nxt = J;\n\n    for (int it = 0; it < n_iter; ++it) {\n        for (int64_t z = 0; z < nz; ++z)\n            for (int64_t y = 0; y < ny; ++y)\n                for (int64_t x = 0; x < nx; ++x) {\n                    const int64_t c[3] = {x, y, z};\n                    const int64_t p = x + nx * (y + ny * z);\n                    double acc",
                        "const int64_t stride[3] = {1, ny, nx * ny};\n    double *cur = I, *nxt = J;\n\n    for (int it = 0; it < n_iter; ++it) {\n        for (int64_t z = 0; z < nz; ++z)\n            for (int64_t y = 0; y < ny; ++y)\n                for (int64_t x = 0; x < nx; ++x) {\n                    const int64_t c[3] = {x, y, z};\n                    const int64_t p = x + nx * (y + ny * z);\n                    double acc"),
     "k_zero_passes_flux": ("if (K == 0.0)\n        return 0.0;", "if (K == 0.0)\n        return 1.0;"),
+    "fdiag_strict_mask": ("const int mo = io >= t_o;", "const int mo = io > t_o;"),
+    "fdiag_filtered_intensity": ("if (mf) {\n                    s_of += io;",
+                                 "if (mf) {\n                    s_of += iff;"),
+    "fdiag_swapped_masks": ("if (mf) {\n                    s_of += io;",
+                            "if (mo) {\n                    s_of += io;"),
 }
 
 
@@ -68,6 +75,10 @@ def pins_hold(lib) -> bool:
                 return False
         c = rng.standard_normal((5, 6, 7))
         if not np.array_equal(f(c, 0.0, 0.125, 5, "rational"), c):
+            return False
+        Io, If, Im = fdiag_hand_cubes()
+        r = oracle.f_diagnostic(Io, If, Im, rms_o=1.0, rms_f=1.0, lib=lib)
+        if (r["S_oo"], r["N_o"], r["S_of"], r["N_f"], r["S_mf"]) != (12.0, 3, 6.5, 4, 6.0):
             return False
     except ValueError:
         return False

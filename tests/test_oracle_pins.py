@@ -341,3 +341,68 @@ def test_storage_formats():
     assert err.max() <= s / 2048 + 1e-7
     assert oracle.pow2_scale(1.0) == 1.0 and oracle.pow2_scale(0.7) == 0.5
     assert oracle.pow2_scale(0.75) == 1.0 and oracle.pow2_scale(3.0) == 4.0
+
+# ------------------------------------------------------- F diagnostics
+def fdiag_hand_cubes():
+    """2x2x2 hand example; rms 1, so both thresholds are 3.  Voxels exactly at
+    3 belong to the masks (eq. "Mfequa": I >= 3 rms)."""
+    Io = np.array([4, 1, 3, 0, -1, 2, 5, 0.5], np.float32).reshape(2, 2, 2)
+    If = np.array([2, 3.5, 1, 3, 0, 0, 6, 3], np.float32).reshape(2, 2, 2)
+    Im = np.array([3, 0, 2, 1, 0, 0, 4, 1], np.float32).reshape(2, 2, 2)
+    return Io, If, Im
+
+
+def test_f_diagnostic_hand_values():
+    Io, If, Im = fdiag_hand_cubes()
+    r = oracle.f_diagnostic(Io, If, Im, rms_o=1.0, rms_f=1.0)
+    # M_o = {4, 3, 5}: S_oo = 12, N_o = 3.  M_f = {3.5, 3, 6, 3} at voxels
+    # 1, 3, 6, 7: S_of = I_o there = 1 + 0 + 5 + 0.5 = 6.5 (Sec. 4: the sums
+    # take the original intensities), N_f = 4.
+    assert (r["S_oo"], r["N_o"], r["S_of"], r["N_f"]) == (12.0, 3, 6.5, 4)
+    assert r["F"] == 6.5 / 12.0
+    # sigma_F^2 = sigma_of^2 / S_oo^2 + S_of^2 sigma_oo^2 / S_oo^4 with
+    # sigma_of = sqrt(4) * 1, sigma_oo = sqrt(3) * 1
+    assert r["sigma_F"] == pytest.approx(math.sqrt(4 / 144 + 6.5 ** 2 * 3 / 12 ** 4), rel=1e-15)
+    # F_M: S_m = 11, S_mf = I_m at 1, 3, 6, 7 = 0 + 1 + 4 + 1 = 6
+    assert (r["S_m"], r["S_mf"], r["F_M"]) == (11.0, 6.0, 6.0 / 11.0)
+    # independent voxels: a beam of 4 voxels divides N_i by 4, sigma_F by 2
+    r4 = oracle.f_diagnostic(Io, If, Im, rms_o=1.0, rms_f=1.0, beam=4.0)
+    assert r4["sigma_F"] == pytest.approx(r["sigma_F"] / 2, rel=1e-15)
+    # another threshold multiple: at 2 rms, M_o = {4, 3, 2, 5} and M_f gains
+    # voxel 0 (I_f = 2, I_o = 4)
+    r2 = oracle.f_diagnostic(Io, If, rms_o=1.0, rms_f=1.0, nsig=2.0)
+    assert (r2["S_oo"], r2["N_o"], r2["S_of"], r2["N_f"]) == (14.0, 4, 10.5, 5)
+
+
+def test_f_diagnostic_invariants():
+    rng = np.random.default_rng(21)
+    Io = (rng.standard_normal((9, 11, 13)) * 1.3).astype(np.float32)
+    Io[3:6, 4:8, 5:9] += 6.0
+    If = (Io + rng.standard_normal(Io.shape).astype(np.float32) * 0.3).astype(np.float32)
+    Im = np.clip(Io, 0, None).astype(np.float32)
+    # unfiltered: F = 1 exactly and both error terms are equal
+    r = oracle.f_diagnostic(Io, Io)
+    assert r["F"] == 1.0 and r["N_f"] == r["N_o"]
+    assert r["sigma_F"] == pytest.approx(math.sqrt(2 * r["N_o"]) * r["rms_o"] / abs(r["S_oo"]),
+                                         rel=1e-14)
+    # default rms: the noise estimate of each full cube
+    r = oracle.f_diagnostic(Io, If, Im)
+    assert r["rms_o"] == oracle.noise_rms(Io) and r["rms_f"] == oracle.noise_rms(If)
+    # power-of-two scaling of every cube (and so of the rms) changes nothing
+    r8 = oracle.f_diagnostic(Io * 8, If * 8, Im * 8)
+    for key in ("F", "sigma_F", "F_M", "N_o", "N_f"):
+        assert r8[key] == r[key], key
+    # a ROI equals the same diagnostic on the cropped cubes with the same rms
+    roi = (2, 10, 1, 9, 3, 7)
+    a = oracle.f_diagnostic(Io, If, Im, roi=roi, rms_o=r["rms_o"], rms_f=r["rms_f"])
+    crop = lambda c: np.ascontiguousarray(c[3:7, 1:9, 2:10])
+    b = oracle.f_diagnostic(crop(Io), crop(If), crop(Im), rms_o=r["rms_o"], rms_f=r["rms_f"])
+    assert a == b
+    # brute force in plain numpy on the whole cube
+    mo, mf = Io >= 3 * r["rms_o"], If >= 3 * r["rms_f"]
+    d = Io.astype(np.float64)
+    assert r["S_oo"] == pytest.approx(math.fsum(d[mo]), rel=1e-13)
+    assert r["S_of"] == pytest.approx(math.fsum(d[mf]), rel=1e-13)
+    assert (r["N_o"], r["N_f"]) == (int(mo.sum()), int(mf.sum()))
+    with pytest.raises(ValueError):
+        oracle.f_diagnostic(Io, If, roi=(0, 0, 0, 1, 0, 1))
