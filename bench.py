@@ -58,9 +58,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["afd", "reference"], default="afd")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--lines", default="paper,precision,batch,serving",
+    ap.add_argument("--lines", default="paper,diagnostics,precision,batch,serving",
                     help="extra lines measured after the headline (N=1 only): any of "
-                         "paper, precision, batch, serving, or 'none'")
+                         "paper, diagnostics, precision, batch, serving, or 'none'")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="arrival window per request rate of the serving line")
     return ap.parse_args()
@@ -313,6 +313,56 @@ def line_paper_form(afd, ctx):
                               "note": "other hardware, other data (NGC 2841); context only"}}
 
 
+def line_diagnostics(afd, ctx, d_in, d_out):
+    """F / F_M diagnostics (Sec. 4, Sec. 5): throughput of the one-pass masked
+    sums on the benchmark cube (original + filtered, 8 B per voxel), and the
+    paper's Tab. 3 parameter grid for the intensity form (C = 5) on the
+    ModelB stand-in, F +- sigma_F and F_M over the faint tail's ROI."""
+    import torch
+    import synth
+    n_vox = d_in.numel()
+    rms_o = afd.afd_noise_rms(ctx, d_in)
+    rms_f = afd.afd_noise_rms(ctx, d_out)
+    call = lambda: afd.afd_f_diagnostic(ctx, d_in, d_out, rms_o=rms_o, rms_f=rms_f)
+    for _ in range(3):
+        call()
+    reps = 30
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        r = call()
+    us = (time.perf_counter() - t0) / reps * 1e6
+    peak, peak_kind = measured_peaks()
+    gbs = 8.0 * n_vox / us / 1e3
+    cube, model, roi = synth.model_b()
+    d_o = torch.from_numpy(cube).to(d_in.device)
+    d_m = torch.from_numpy(model).to(d_in.device)
+    d_f = torch.empty_like(d_o)
+    rms = afd.afd_noise_rms(ctx, d_o)
+    grid = [(0.5, 0.0325, 20), (0.5, 0.0625, 20), (0.5, 0.0325, 30), (0.5, 0.0625, 30),
+            (1.0, 0.0325, 20), (1.0, 0.0325, 30), (1.5, 0.0325, 20), (1.5, 0.0325, 30),
+            (2.0, 0.0325, 20), (2.0, 0.0325, 30)]
+    rows = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for K, tau, n in grid:
+        afd.afd_filter_intensity(ctx, d_o, d_f, K, rms, tau, n, (5.0, 5.0, 5.0))
+        q = afd.afd_f_diagnostic(ctx, d_o, d_f, d_m, roi=roi)
+        rows.append({"K": K, "tau": tau, "n": n, "F": q["F"], "sigma_F": q["sigma_F"],
+                     "F_M": q["F_M"]})
+    sweep_ms = (time.perf_counter() - t0) * 1e3
+    return {"fdiag": {"workload": "masked F sums over the benchmark cube and its 50-iteration "
+                                  "result (268 MB each), rms given, synchronous call",
+                      "us_per_call": us, "algorithmic_GBs": gbs, "peak_GBs": peak,
+                      "frac": gbs / peak, "peak_kind": peak_kind, "F": r["F"],
+                      "N_o": r["N_o"], "N_f": r["N_f"]},
+            "tab3_sweep": {"workload": "intensity form, C = 5, the (K, tau, n) grid of the "
+                                       "paper's Tab. 3, on the ModelB stand-in (104x104x64, "
+                                       "disk of peak SNR 32 + a 0.75-sigma tail, unit noise, "
+                                       "seed 0); F, sigma_F and F_M over the tail's ROI "
+                                       + str(roi),
+                           "runs": rows, "ms_total": sweep_ms}}
+
+
 def line_batch(afd, ctx):
     """300 galaxy cutouts of uneven size, K_i = 1.5 sigma_i (GPU FP64 noise
     estimate), 20 iterations, one CUDA-graph launch per call; z-chunk picked
@@ -530,6 +580,8 @@ def run_afd(args):
         want = set(args.lines.split(","))
         if "paper" in want:
             lines["paper"] = line_paper_form(afd, ctx)
+        if "diagnostics" in want:
+            lines["diagnostics"] = line_diagnostics(afd, ctx, d_in, d_out)
         if "precision" in want:
             lines["precision"] = line_precision(afd, ctx, cube, d_in, d_out, sig)
         if "batch" in want:

@@ -273,6 +273,38 @@ afd_status afd_sum(afd_ctx *ctx, const float *cube, int64_t n, double *out);
  * expired (the error word is then cleared). */
 afd_status afd_sync(afd_ctx *ctx);
 
+/* The paper's smoothing-quality diagnostic F (Sec. 4, eqs. "F_equa",
+ * "Sequa", "Mfequa") and recovered-signal fraction F_M (Sec. 5, eq.
+ * "sums_equa") of a filtered cube against its original, over a ROI box.
+ *   masks:  M_o = [I_o >= nsig rms_o],  M_f = [I_f >= nsig rms_f]  (nsig = 3
+ *           in the paper)
+ *   sums (always of the ORIGINAL intensities, or of the model's):
+ *           S_of = sum I_o M_f, S_oo = sum I_o M_o, S_mf = sum I_m M_f,
+ *           S_m = sum I_m
+ *   F = |S_of| / |S_oo|;  F_M = |S_mf| / |S_m| (NaN without a model);
+ *   sigma_F = sqrt(s_of^2 / S_oo^2 + S_of^2 s_oo^2 / S_oo^4) with
+ *           s_oi = sqrt(N_i / beam) rms_i, N_i the voxels in mask i and beam
+ *           the voxels per independent element (1: uncorrelated noise). */
+typedef struct {
+    double S_of, S_oo, S_mf, S_m;
+    int64_t N_o, N_f;
+    double rms_o, rms_f; /* the noise levels used */
+    double F, sigma_F, F_M;
+} afd_fdiag;
+
+/* orig, filt, model: DEVICE float32 cubes of one shape (model may be NULL).
+ * roi: HOST array {x0, x1, y0, y1, z0, z1} (half-open, inside the cube; NULL
+ * = the whole cube).  rms_o / rms_f <= 0: estimated as afd_noise_rms of the
+ * full cube (Sec. 4 takes the rms constant over the cube).  The mask
+ * decisions are exact (thresholds rounded up to the next float); the sums
+ * are accurate to a few float32 ulps of the summed magnitudes.  Synchronous:
+ * *out (HOST) is filled on return.  AFD_EINVAL for an empty or out-of-range
+ * box, nsig not finite and > 0, beam < 1 or not finite, or a NaN/inf rms. */
+afd_status afd_f_diagnostic(afd_ctx *ctx, const float *orig, const float *filt,
+                            const float *model, int64_t nx, int64_t ny, int64_t nz,
+                            const int64_t *roi, double rms_o, double rms_f, double nsig,
+                            double beam, afd_fdiag *out);
+
 /* Pass timing, for profiling: while on, every float32 filter call that runs
  * on the streaming kernel records a pair of CUDA events on the context's
  * stream around its sequence of passes (after the statistics of

@@ -50,6 +50,8 @@ def _load():
         "afd_filter_host": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_host_async": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_rel": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int, vp], c_int),
+        "afd_f_diagnostic": ([vp, vp, vp, vp, i64, i64, i64, vp, ctypes.c_double,
+                              ctypes.c_double, ctypes.c_double, ctypes.c_double, vp], c_int),
         "afd_pass_timing": ([vp, c_int], c_int),
         "afd_pass_timing_read": ([vp, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int64)], c_int),
@@ -262,6 +264,39 @@ def afd_filter_rel(ctx: Context, cube_in: torch.Tensor, cube_out: torch.Tensor, 
                                float(k_rms), float(dt), int(n_iter), COND[conductance], kp),
            "afd_filter_rel", ctx)
     return cube_out
+
+
+class FDiag(ctypes.Structure):
+    _fields_ = [("S_of", ctypes.c_double), ("S_oo", ctypes.c_double),
+                ("S_mf", ctypes.c_double), ("S_m", ctypes.c_double),
+                ("N_o", ctypes.c_int64), ("N_f", ctypes.c_int64),
+                ("rms_o", ctypes.c_double), ("rms_f", ctypes.c_double),
+                ("F", ctypes.c_double), ("sigma_F", ctypes.c_double),
+                ("F_M", ctypes.c_double)]
+
+
+def afd_f_diagnostic(ctx: Context, orig: torch.Tensor, filt: torch.Tensor,
+                     model: torch.Tensor | None = None, roi=None, rms_o: float = 0.0,
+                     rms_f: float = 0.0, nsig: float = 3.0, beam: float = 1.0) -> dict:
+    """F, sigma_F and F_M (and the sums behind them) of a filtered cube
+    against its original over roi = (x0, x1, y0, y1, z0, z1); rms <= 0 means
+    estimate it on the full cube."""
+    cubes = [orig, filt] + ([model] if model is not None else [])
+    for t in cubes:
+        if not t.is_cuda or t.dtype != torch.float32 or t.shape != orig.shape:
+            raise ValueError("CUDA float32 cubes of one shape expected")
+    p_o, nx, ny, nz = _cube_args(orig)
+    p_f, _, _, _ = _cube_args(filt)
+    p_m = _cube_args(model)[0] if model is not None else None
+    box = None
+    if roi is not None:
+        box = (ctypes.c_int64 * 6)(*[int(v) for v in roi])
+    _use_current_stream(ctx, orig)
+    r = FDiag()
+    _check(_lib.afd_f_diagnostic(ctx.handle, p_o, p_f, p_m, nx, ny, nz, box, float(rms_o),
+                                 float(rms_f), float(nsig), float(beam), ctypes.byref(r)),
+           "afd_f_diagnostic", ctx)
+    return {name: getattr(r, name) for name, _ in FDiag._fields_}
 
 
 def afd_pass_timing(ctx: Context, on: bool) -> None:

@@ -504,6 +504,8 @@ afd_status afd_destroy(afd_ctx *ctx)
     }
     if (ctx->scratch)
         cudaFree(ctx->scratch);
+    if (ctx->fd_buf)
+        cudaFree(ctx->fd_buf);
     if (ctx->lp_scratch)
         cudaFree(ctx->lp_scratch);
     if (ctx->fb_scratch)
@@ -623,6 +625,87 @@ afd_status afd_filter_rel(afd_ctx *ctx, const float *in, float *out, int64_t nx,
     if (e != cudaSuccess)
         return cuda_fail(ctx, e);
     return run_passes(ctx, in, out, nx, ny, nz, kind, b, n_iter, ctx->d_coef);
+}
+
+namespace {
+// The smallest float >= t (so that, for a float I, I >= t exactly when
+// I >= the result).
+float float_at_or_above(double t)
+{
+    float f = static_cast<float>(t);
+    if (static_cast<double>(f) < t)
+        f = std::nextafter(f, INFINITY);
+    return f;
+}
+}  // namespace
+
+afd_status afd_f_diagnostic(afd_ctx *ctx, const float *orig, const float *filt,
+                            const float *model, int64_t nx, int64_t ny, int64_t nz,
+                            const int64_t *roi, double rms_o, double rms_f, double nsig,
+                            double beam, afd_fdiag *out)
+{
+    if (!ctx || !orig || !filt || !out || !dims_ok(nx, ny, nz) || !(nsig > 0.0) ||
+        !std::isfinite(nsig) || !(beam >= 1.0) || !std::isfinite(beam) || std::isnan(rms_o) ||
+        std::isnan(rms_f) || std::isinf(rms_o) || std::isinf(rms_f))
+        return AFD_EINVAL;
+    int64_t box[6] = {0, nx, 0, ny, 0, nz};
+    if (roi)
+        for (int i = 0; i < 6; ++i)
+            box[i] = roi[i];
+    if (box[0] < 0 || box[1] > nx || box[0] >= box[1] || box[2] < 0 || box[3] > ny ||
+        box[2] >= box[3] || box[4] < 0 || box[5] > nz || box[4] >= box[5])
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    const int64_t n = nx * ny * nz;
+    // noise levels: given, or the estimate of each full cube (Sec. 4 assumes
+    // the rms constant over the cube)
+    if (rms_o <= 0.0 && (st = afd_noise_rms(ctx, orig, n, &rms_o)) != AFD_OK)
+        return st;
+    if (rms_f <= 0.0 && (st = afd_noise_rms(ctx, filt, n, &rms_f)) != AFD_OK)
+        return st;
+    const size_t part_bytes = static_cast<size_t>(ctx->part_blocks) * 6 * sizeof(double);
+    st = ensure_buffer(ctx, &ctx->fd_buf, &ctx->fd_bytes, part_bytes + 6 * sizeof(double));
+    if (st != AFD_OK)
+        return st;
+    double *part = reinterpret_cast<double *>(ctx->fd_buf);
+    double *out6 = part + static_cast<size_t>(ctx->part_blocks) * 6;
+    const int box32[6] = {static_cast<int>(box[0]), static_cast<int>(box[1]),
+                          static_cast<int>(box[2]), static_cast<int>(box[3]),
+                          static_cast<int>(box[4]), static_cast<int>(box[5])};
+    const float t_o = float_at_or_above(nsig * rms_o);
+    const float t_f = float_at_or_above(nsig * rms_f);
+    cudaError_t e = afd::launch_fdiag(orig, filt, model, nx, ny, box32, t_o, t_f, part,
+                                      ctx->part_blocks, out6, ctx->stream);
+    ctx->launches += 2;
+    double h[6];
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h, out6, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    afd_fdiag r;
+    r.S_of = h[0];
+    r.S_oo = h[1];
+    r.S_mf = h[2];
+    r.S_m = h[3];
+    r.N_o = static_cast<int64_t>(h[4]);
+    r.N_f = static_cast<int64_t>(h[5]);
+    r.rms_o = rms_o;
+    r.rms_f = rms_f;
+    const double nan = std::nan("");
+    r.F = r.S_oo != 0.0 ? std::fabs(r.S_of) / std::fabs(r.S_oo) : nan;
+    const double sig_of = std::sqrt(static_cast<double>(r.N_f) / beam) * rms_f;
+    const double sig_oo = std::sqrt(static_cast<double>(r.N_o) / beam) * rms_o;
+    r.sigma_F = r.S_oo != 0.0 ? std::sqrt(sig_of * sig_of / (r.S_oo * r.S_oo) +
+                                          r.S_of * r.S_of * sig_oo * sig_oo /
+                                              (r.S_oo * r.S_oo * r.S_oo * r.S_oo))
+                              : nan;
+    r.F_M = (model && r.S_m != 0.0) ? std::fabs(r.S_mf) / std::fabs(r.S_m) : nan;
+    *out = r;
+    return AFD_OK;
 }
 
 afd_status afd_filter_intensity(afd_ctx *ctx, const float *in, float *out, int64_t nx,

@@ -44,6 +44,8 @@ struct afd_ctx {
     int part_blocks = 0;
     double *d_out4 = nullptr;    // stats result (device)
     afd::Coef *d_coef = nullptr; // coefficients computed on the device (afd_filter_rel)
+    float *fd_buf = nullptr;     // F diagnostic: block partials + result (doubles)
+    size_t fd_bytes = 0;
     double *h_out4 = nullptr;    // stats result (pinned host)
     uint64_t launches = 0;
     // pass timing (afd_pass_timing): event pairs around each pass sequence

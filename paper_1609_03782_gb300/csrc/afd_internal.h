@@ -146,6 +146,13 @@ cudaError_t launch_dequantize(int S, const void *in, float *out, int64_t n, floa
 // ---- FP64 statistics -------------------------------------------------------
 constexpr int kStatsThreads = 256;
 // partials: 4 doubles per block; out4: sum, sum sq, negative sum sq, count
+// F diagnostic sums over the ROI box roi = {x0, x1, y0, y1, z0, z1} of cubes
+// with row pitch nx and ny rows per plane: out6 = {S_of, S_oo, S_mf, S_m, N_o,
+// N_f} (device doubles; im may be null).  t_o, t_f: float thresholds already
+// rounded up from nsig x rms.  part: nblocks x 6 doubles of scratch.
+cudaError_t launch_fdiag(const float *io, const float *iff, const float *im, int64_t nx,
+                         int64_t ny, const int roi[6], float t_o, float t_f, double *part,
+                         int nblocks, double *out6, cudaStream_t stream);
 // Noise-relative coefficients: from launch_stats' out4, K = k_rms x rms
 // (rms of the negative voxels) and the coefficients of conductance `kind`
 // into *coef (device); A on the device, the B terms taken from b (host

@@ -29,6 +29,9 @@ The named workloads:
 ``cube2048``   2048 x 2048 x 256, 60 disks + 10 tails, seed 0
 ``cutouts``    300 cutouts, nx, ny ~ U{32..256}, nz ~ U{32..128}, 1 disk each
 ``serving``    64 resident cubes: 21 x 128^3, 21 x 256^3, 22 x 512x512x128
+``model_b``    104 x 104 x 64 (6.9e5 voxels, the size of the paper's model
+               galaxies): one disk of peak SNR 32 + a faint tail (0.75 sigma),
+               returned with its noiseless model and the tail's ROI box
 =============  ==============================================================
 """
 from __future__ import annotations
@@ -233,3 +236,26 @@ def noiseless_disk64() -> np.ndarray:
     add_disk(cube, 32.0 + rng.uniform(-2, 2), 32.0 + rng.uniform(-2, 2),
              60.0, rng.uniform(0.0, 180.0), 32.0)
     return cube
+
+
+def model_b(seed: int = 0):
+    """A stand-in for the paper's ModelB noise study (Sec. 5): the noiseless
+    model (one disk, peak SNR 32, and a faint tail of amplitude 0.75 sigma),
+    the same plus unit noise, and the ROI box (x0, x1, y0, y1, z0, z1) around
+    the tail.  Returns (cube, model, roi); cube = noise + model in float32."""
+    shape = (64, 104, 104)
+    nz, ny, nx = shape
+    rng = rng_for(seed)
+    cube = noise(shape, rng)
+    model = np.zeros(shape, dtype=np.float32)
+    add_disk(model, 40.0, 52.0, 55.0, rng.uniform(0.0, 180.0), nz / 2.0, amp=32.0)
+    ctrl = np.array([[62.0, 20.0, 20.0], [78.0, 40.0, 26.0], [88.0, 66.0, 34.0],
+                     [92.0, 90.0, 40.0]])
+    add_tail(model, ctrl, 0.75 * SIGMA)
+    cube += model
+    pad = int(math.ceil(3.5 * SIGMA_T))
+    lo = np.maximum(np.floor(ctrl.min(axis=0)).astype(int) - pad, 0)
+    hi = np.minimum(np.ceil(ctrl.max(axis=0)).astype(int) + pad + 1, [nx, ny, nz])
+    roi = (int(lo[0]), int(hi[0]), int(lo[1]), int(hi[1]), int(lo[2]), int(hi[2]))
+    return cube, model, roi
+
