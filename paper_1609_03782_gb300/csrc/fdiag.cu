@@ -10,8 +10,9 @@
 // The thresholds arrive as floats already rounded up from nsig x rms (the
 // smallest float >= the exact threshold), so a float comparison takes the
 // same mask decision as the exact one.  Each warp walks rows of the box
-// (lanes along x, four elements per lane per step, all loads issued before
-// they are used); a lane's four values are summed in float32 and the sums
+// (lanes along x; float4 loads when the rows are 16-byte aligned, else four
+// scalars per lane per step; all loads issued before they are used); a
+// lane's four values are summed in float32 and the sums
 // added to float-float (TwoSum) accumulators, converted to double once per
 // thread.  Warps and blocks combine in double in a fixed order, so a result
 // is reproducible for a given grid.  HBM-bound: 8 (12 with the model) bytes
@@ -39,7 +40,27 @@ struct FFsum {
     }
 };
 
+// One element's contribution to the four partial sums and two counts.
 template <bool MODEL>
+__device__ __forceinline__ void fd_term(bool in, float vo, float vf, float vm, float t_o,
+                                        float t_f, float &a_of, float &a_oo, float &a_mf,
+                                        float &a_m, int &n_o, int &n_f)
+{
+    const bool mo = in && vo >= t_o;
+    const bool mf = in && vf >= t_f;
+    a_oo = __fadd_rn(a_oo, mo ? vo : 0.0f);
+    a_of = __fadd_rn(a_of, mf ? vo : 0.0f);
+    n_o += mo ? 1 : 0;
+    n_f += mf ? 1 : 0;
+    if (MODEL) {
+        a_m = __fadd_rn(a_m, in ? vm : 0.0f);
+        a_mf = __fadd_rn(a_mf, mf ? vm : 0.0f);
+    }
+}
+
+// VEC: rows start 16-byte aligned and hold a multiple of 4 elements; each
+// lane then loads float4s (two per cube per step), else four scalars.
+template <bool MODEL, bool VEC>
 __global__ void __launch_bounds__(kFdThreads)
     fdiag_partial(const float *__restrict__ io_, const float *__restrict__ if_,
                   const float *__restrict__ im_, int64_t nx, int64_t ny, int x0, int x1, int y0,
@@ -57,6 +78,44 @@ __global__ void __launch_bounds__(kFdThreads)
         const int64_t z = z0 + r / nyr;
         const int64_t y = y0 + (r - (r / nyr) * nyr);
         const int64_t base = x0 + nx * (y + ny * z);
+        if (VEC) {
+            const float4 *po = reinterpret_cast<const float4 *>(io_ + base);
+            const float4 *pf = reinterpret_cast<const float4 *>(if_ + base);
+            const float4 *pm = MODEL ? reinterpret_cast<const float4 *>(im_ + base) : nullptr;
+            const int L4 = L / 4;
+            for (int q = lane; q < L4; q += 64) {
+                float4 vo[2], vf[2], vm[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const bool in = q + 32 * k < L4;
+                    const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    vo[k] = in ? __ldcs(po + q + 32 * k) : zero;
+                    vf[k] = in ? __ldcs(pf + q + 32 * k) : zero;
+                    if (MODEL)
+                        vm[k] = in ? __ldcs(pm + q + 32 * k) : zero;
+                }
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const bool in = q + 32 * k < L4;
+                    float a_of = 0.0f, a_oo = 0.0f, a_mf = 0.0f, a_m = 0.0f;
+                    fd_term<MODEL>(in, vo[k].x, vf[k].x, vm[k].x, t_o, t_f, a_of, a_oo, a_mf, a_m,
+                                   n_o, n_f);
+                    fd_term<MODEL>(in, vo[k].y, vf[k].y, vm[k].y, t_o, t_f, a_of, a_oo, a_mf, a_m,
+                                   n_o, n_f);
+                    fd_term<MODEL>(in, vo[k].z, vf[k].z, vm[k].z, t_o, t_f, a_of, a_oo, a_mf, a_m,
+                                   n_o, n_f);
+                    fd_term<MODEL>(in, vo[k].w, vf[k].w, vm[k].w, t_o, t_f, a_of, a_oo, a_mf, a_m,
+                                   n_o, n_f);
+                    s_of.add(a_of);
+                    s_oo.add(a_oo);
+                    if (MODEL) {
+                        s_mf.add(a_mf);
+                        s_m.add(a_m);
+                    }
+                }
+            }
+            continue;
+        }
         for (int x = lane; x < L; x += 128) {
             float vo[4], vf[4], vm[4];
 #pragma unroll
@@ -70,19 +129,9 @@ __global__ void __launch_bounds__(kFdThreads)
             }
             float a_of = 0.0f, a_oo = 0.0f, a_mf = 0.0f, a_m = 0.0f;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const bool in = x + 32 * k < L;
-                const bool mo = in && vo[k] >= t_o;
-                const bool mf = in && vf[k] >= t_f;
-                a_oo = __fadd_rn(a_oo, mo ? vo[k] : 0.0f);
-                a_of = __fadd_rn(a_of, mf ? vo[k] : 0.0f);
-                n_o += mo ? 1 : 0;
-                n_f += mf ? 1 : 0;
-                if (MODEL) {
-                    a_m = __fadd_rn(a_m, vm[k]);
-                    a_mf = __fadd_rn(a_mf, mf ? vm[k] : 0.0f);
-                }
-            }
+            for (int k = 0; k < 4; ++k)
+                fd_term<MODEL>(x + 32 * k < L, vo[k], vf[k], MODEL ? vm[k] : 0.0f, t_o, t_f, a_of,
+                               a_oo, a_mf, a_m, n_o, n_f);
             s_of.add(a_of);
             s_oo.add(a_oo);
             if (MODEL) {
@@ -147,12 +196,25 @@ cudaError_t launch_fdiag(const float *io, const float *iff, const float *im, int
                          int64_t ny, const int roi[6], float t_o, float t_f, double *part,
                          int nblocks, double *out6, cudaStream_t stream)
 {
-    if (im)
-        fdiag_partial<true><<<nblocks, kFdThreads, 0, stream>>>(
-            io, iff, im, nx, ny, roi[0], roi[1], roi[2], roi[3], roi[4], roi[5], t_o, t_f, part);
-    else
-        fdiag_partial<false><<<nblocks, kFdThreads, 0, stream>>>(
-            io, iff, im, nx, ny, roi[0], roi[1], roi[2], roi[3], roi[4], roi[5], t_o, t_f, part);
+    auto al16 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    const bool vec = (nx % 4) == 0 && (roi[0] % 4) == 0 && ((roi[1] - roi[0]) % 4) == 0 &&
+                     al16(io) && al16(iff) && (!im || al16(im));
+#define FD_LAUNCH(M, V)                                                                     \
+    fdiag_partial<M, V><<<nblocks, kFdThreads, 0, stream>>>(io, iff, im, nx, ny, roi[0], roi[1], \
+                                                             roi[2], roi[3], roi[4], roi[5], t_o, \
+                                                             t_f, part)
+    if (im) {
+        if (vec)
+            FD_LAUNCH(true, true);
+        else
+            FD_LAUNCH(true, false);
+    } else {
+        if (vec)
+            FD_LAUNCH(false, true);
+        else
+            FD_LAUNCH(false, false);
+    }
+#undef FD_LAUNCH
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
