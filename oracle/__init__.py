@@ -25,6 +25,9 @@ stats / noise_rms    FP64 sums and the negative-half noise estimate (K is set
 quantize/dequantize  2-byte storage formats with a power-of-two per-cube scale
 f_diagnostic         the smoothing-quality parameter F with its error sigma_F
                      (Sec. 4) and the recovered-signal fraction F_M (Sec. 5)
+box_weights /        the box and (rotated) Gaussian kernels of Sec. 3.1 and
+gauss_weights        3.2, and smooth, the normalised correlation with them
+smooth
 """
 from __future__ import annotations
 
@@ -74,6 +77,9 @@ def load_library(path: str):
     lib.orc_stats.argtypes = [vp, i64, vp]
     lib.orc_fdiag.argtypes = [vp, vp, vp, i64, i64, i64, vp, dbl, dbl, vp]
     lib.orc_fdiag.restype = ctypes.c_int
+    lib.orc_smooth.argtypes = [vp, vp, i64, i64, i64, vp, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int]
+    lib.orc_smooth.restype = ctypes.c_int
     lib.orc_stats.restype = None
     return lib
 
@@ -213,6 +219,72 @@ def f_diagnostic(orig, filt, model=None, roi=None, rms_o=None, rms_f=None, nsig=
                     if s_oo != 0.0 else math.nan)
     r["F_M"] = (abs(s_mf) / abs(s_m) if (Im is not None and s_m != 0.0) else math.nan)
     return r
+
+
+# --------------------------------------------------------------------------
+# Box and Gaussian smoothing (Sec. 3.1, 3.2).  Weight arrays are (nz, ny, nx)
+# shaped like the cubes: W[dz + rz, dy + ry, dx + rx].
+# --------------------------------------------------------------------------
+FWHM_PER_SIGMA = 2.0 * math.sqrt(2.0 * math.log(2.0))   # FWHM_i = 2 sqrt(2 ln 2) sigma_i
+
+
+def box_weights(n) -> np.ndarray:
+    """The box (mean) filter's kernel: N_x x N_y x N_z ones, sizes odd so the
+    window is centred on the voxel (Sec. 3.1; Tab. 1 uses odd sizes)."""
+    nx_, ny_, nz_ = (int(v) for v in n)
+    if min(nx_, ny_, nz_) < 1 or not (nx_ % 2 and ny_ % 2 and nz_ % 2):
+        raise ValueError("box sizes must be odd and positive")
+    return np.ones((nz_, ny_, nx_), dtype=np.float64)
+
+
+def rotation(angles_deg) -> np.ndarray:
+    """R = R_z(theta_z) R_y(theta_y) R_x(theta_x), the Euler rotation of the
+    Gaussian kernel (Sec. 3.2), angles in degrees, right-handed."""
+    ax, ay, az = (math.radians(float(a)) for a in angles_deg)
+    cx, sx, cy, sy, cz, sz = (math.cos(ax), math.sin(ax), math.cos(ay), math.sin(ay),
+                              math.cos(az), math.sin(az))
+    Rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+    Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+    Rz = np.array([[cz, -sz, 0], [sz, cz, 0], [0, 0, 1]])
+    return Rz @ Ry @ Rx
+
+
+def gauss_weights(fwhm, angles_deg=(0.0, 0.0, 0.0), truncate: float = 3.0) -> np.ndarray:
+    """The Gaussian kernel of Sec. 3.2: G = exp(-sum_i (x_i)^2 / (2 sigma_i^2))
+    with sigma_i = FWHM_i / (2 sqrt(2 ln 2)), rotated by R (K(p) = G(R^T p)),
+    sampled at integer offsets and truncated where the ellipsoid's extent
+    along each axis passes truncate sigma: r_a = ceil(truncate sqrt(Sigma_aa)),
+    Sigma = R diag(sigma^2) R^T.  Unnormalised (smooth() divides by the
+    in-cube weight)."""
+    sig = np.array([float(f) / FWHM_PER_SIGMA for f in fwhm])
+    if np.any(sig <= 0.0):
+        raise ValueError("FWHM must be positive")
+    R = rotation(angles_deg)
+    cov = R @ np.diag(sig ** 2) @ R.T
+    r = [int(math.ceil(truncate * math.sqrt(cov[a, a]) - 1e-12)) for a in range(3)]
+    dz, dy, dx = np.meshgrid(np.arange(-r[2], r[2] + 1), np.arange(-r[1], r[1] + 1),
+                             np.arange(-r[0], r[0] + 1), indexing="ij")
+    p = np.stack([dx, dy, dz], axis=-1).astype(np.float64)     # (x, y, z) offsets
+    u = p @ R                                                  # R^T p, per offset
+    return np.exp(-0.5 * np.sum((u / sig) ** 2, axis=-1))
+
+
+def smooth(cube, weights, lib=None) -> np.ndarray:
+    """Normalised correlation of the cube with the weight array (odd sizes):
+    out(p) = sum W(q - p) I(q) / sum W(q - p) over the window inside the cube
+    (float64 result)."""
+    a = np.ascontiguousarray(cube, dtype=np.float32)
+    nx, ny, nz = _shape3(a)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    wz, wy, wx = w.shape
+    if not (wz % 2 and wy % 2 and wx % 2):
+        raise ValueError("weight array sizes must be odd")
+    out = np.empty((nz, ny, nx), dtype=np.float64)
+    rc = (lib or _load()).orc_smooth(out.ctypes.data, a.ctypes.data, nx, ny, nz, w.ctypes.data,
+                                     wx // 2, wy // 2, wz // 2)
+    if rc != 0:
+        raise ValueError("oracle smooth rejected its arguments")
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -240,3 +240,50 @@ int orc_fdiag(const float *Io, const float *If, const float *Im, int64_t nx, int
     out[5] = n_f;
     return 0;
 }
+
+/*
+ * Smoothing by a normalised correlation (the box and Gaussian filters of
+ * Sec. 3.1 and 3.2):
+ *   out(p) = sum_q W(q - p) I(q) / sum_q W(q - p),
+ * q over the (2rx+1) x (2ry+1) x (2rz+1) window around p that lies inside
+ * the cube.  W is given explicitly (x fastest, index dx+rx + (2rx+1) *
+ * (dy+ry + (2ry+1) * (dz+rz))).  The paper states no boundary rule; dividing
+ * by the in-cube weight makes the box filter the mean of the existing
+ * neighbours ("the mean value of its neighbors, including itself") and keeps
+ * a constant cube constant.  Returns -1 for a bad radius, or when the
+ * in-cube weight of some voxel is not positive.
+ */
+int orc_smooth(double *out, const float *I, int64_t nx, int64_t ny, int64_t nz, const double *W,
+               int rx, int ry, int rz)
+{
+    if (rx < 0 || ry < 0 || rz < 0)
+        return -1;
+    const int64_t wx = 2 * rx + 1, wy = 2 * ry + 1;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                double num = 0.0, den = 0.0;
+                for (int dz = -rz; dz <= rz; ++dz) {
+                    const int64_t qz = z + dz;
+                    if (qz < 0 || qz >= nz)
+                        continue;
+                    for (int dy = -ry; dy <= ry; ++dy) {
+                        const int64_t qy = y + dy;
+                        if (qy < 0 || qy >= ny)
+                            continue;
+                        for (int dx = -rx; dx <= rx; ++dx) {
+                            const int64_t qx = x + dx;
+                            if (qx < 0 || qx >= nx)
+                                continue;
+                            const double w = W[(dx + rx) + wx * ((dy + ry) + wy * (dz + rz))];
+                            num += w * (double)I[qx + nx * (qy + ny * qz)];
+                            den += w;
+                        }
+                    }
+                }
+                if (!(den > 0.0))
+                    return -1;
+                out[x + nx * (y + ny * z)] = num / den;
+            }
+    return 0;
+}

@@ -5,7 +5,8 @@ planted (a dropped axis, a flipped difference, a wrong conductance, a missing
 spacing factor, an in-place Gauss-Seidel sweep, an extra iteration, a
 Dirichlet instead of a zero-flux boundary, a wrong stride, a wrong exponent;
 for the F diagnostic a strict mask threshold, the filtered intensities in
-S_of, and the original mask in place of the filtered one).
+S_of, and the original mask in place of the filtered one; for smoothing a
+window one tap short and transposed weights).
 It is compiled on the CPU into a temporary library and run through the same
 pins as ``test_oracle_pins.py``; at least one pin must fail for every mutant.
 """
@@ -18,7 +19,8 @@ import numpy as np
 import pytest
 
 import oracle
-from test_oracle_pins import fdiag_hand_cubes, frac_pm_facewise, heat_closed_form, impulse
+from test_oracle_pins import (fdiag_hand_cubes, frac_pm_facewise, heat_closed_form, impulse,
+                              smooth_library)
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "afd_oracle.c")
 
@@ -46,6 +48,10 @@ MUTANTS = {
                                  "if (mf) {\n                    s_of += iff;"),
     "fdiag_swapped_masks": ("if (mf) {\n                    s_of += io;",
                             "if (mo) {\n                    s_of += io;"),
+    "smooth_window_short": ("for (int dx = -rx; dx <= rx; ++dx) {",
+                            "for (int dx = -rx; dx < rx; ++dx) {"),
+    "smooth_transposed_weights": ("const double w = W[(dx + rx) + wx * ((dy + ry) + wy * (dz + rz))];",
+                                  "const double w = W[(dy + ry) + wx * ((dx + rx) + wy * (dz + rz))];"),
 }
 
 
@@ -75,6 +81,11 @@ def pins_hold(lib) -> bool:
                 return False
         c = rng.standard_normal((5, 6, 7))
         if not np.array_equal(f(c, 0.0, 0.125, 5, "rational"), c):
+            return False
+        cs = rng.standard_normal((6, 7, 8)).astype(np.float32)
+        ws = oracle.gauss_weights((3.0, 3.0, 2.0), (30.0, 0.0, 0.0))  # rx = ry, not x-y symmetric
+        ref = smooth_library(cs, ws)
+        if not np.allclose(oracle.smooth(cs, ws, lib=lib), ref, rtol=0, atol=1e-13):
             return False
         Io, If, Im = fdiag_hand_cubes()
         r = oracle.f_diagnostic(Io, If, Im, rms_o=1.0, rms_f=1.0, lib=lib)

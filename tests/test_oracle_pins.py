@@ -406,3 +406,68 @@ def test_f_diagnostic_invariants():
     assert (r["N_o"], r["N_f"]) == (int(mo.sum()), int(mf.sum()))
     with pytest.raises(ValueError):
         oracle.f_diagnostic(Io, If, roi=(0, 0, 0, 1, 0, 1))
+
+
+# ------------------------------------------------------- box / Gaussian smoothing
+def smooth_library(cube, w):
+    """The same normalised correlation through scipy.ndimage: zero-padded
+    correlation divided by the zero-padded correlation of ones."""
+    nd = pytest.importorskip("scipy.ndimage")
+    c = np.asarray(cube, dtype=np.float64)
+    return nd.correlate(c, w, mode="constant") / nd.correlate(np.ones_like(c), w, mode="constant")
+
+
+def test_box_hand_values():
+    c = np.arange(4 * 5 * 6, dtype=np.float32).reshape(4, 5, 6)   # value = x + 6y + 30z
+    r = oracle.smooth(c, oracle.box_weights((3, 3, 3)))
+    # interior: the mean of a linear field over a centred window is its centre value
+    assert r[2, 2, 2] == c[2, 2, 2]
+    # corner (0,0,0): the mean over the 2x2x2 in-cube block = 0.5 + 3 + 15
+    assert r[0, 0, 0] == pytest.approx(18.5, abs=1e-12)
+    # a 1x1x1 box is the identity; a 1-D box averages along its axis only
+    assert np.array_equal(oracle.smooth(c, oracle.box_weights((1, 1, 1))), c)
+    r = oracle.smooth(c, oracle.box_weights((5, 1, 1)))
+    assert r[1, 1, 0] == pytest.approx((c[1, 1, 0] + c[1, 1, 1] + c[1, 1, 2]) / 3, abs=1e-12)
+    with pytest.raises(ValueError):
+        oracle.box_weights((2, 3, 3))
+
+
+def test_gauss_kernel_definition():
+    # FWHM: the profile falls to one half at FWHM / 2 (FWHM = 2 sqrt(2 ln 2) sigma)
+    w = oracle.gauss_weights((2.0, 2.0, 2.0))
+    rz, ry, rx = (s // 2 for s in w.shape)
+    assert w[rz, ry, rx] == 1.0
+    assert w[rz, ry, rx + 1] == pytest.approx(0.5, abs=1e-15)
+    # truncation at 3 sigma: sigma = 2 / 2.3548 = 0.849 -> r = ceil(2.548) = 3
+    assert w.shape == (7, 7, 7)
+    # axis-aligned: the outer product of three 1-D Gaussians
+    w = oracle.gauss_weights((3.0, 5.0, 1.5))
+    sig = np.array([3.0, 5.0, 1.5]) / oracle.FWHM_PER_SIGMA
+    g = [np.exp(-0.5 * (np.arange(-(n // 2), n // 2 + 1) / s) ** 2)
+         for n, s in zip(w.shape[::-1], sig)]
+    assert np.allclose(w, g[2][:, None, None] * g[1][None, :, None] * g[0][None, None, :],
+                       rtol=1e-14, atol=0)
+    # rotation by 90 degrees about z swaps the x and y widths
+    a = oracle.gauss_weights((3.0, 5.0, 2.0), (0.0, 0.0, 90.0))
+    b = oracle.gauss_weights((5.0, 3.0, 2.0))
+    assert a.shape == b.shape and np.allclose(a, b, rtol=1e-12, atol=1e-15)
+    # R = Rz Ry Rx: a rotation about z maps x to (cos, sin, 0)
+    R = oracle.rotation((0.0, 0.0, 30.0))
+    assert np.allclose(R @ [1, 0, 0], [math.cos(math.radians(30)), math.sin(math.radians(30)), 0])
+    assert np.allclose(oracle.rotation((10, 20, 30)) @ oracle.rotation((10, 20, 30)).T, np.eye(3))
+
+
+def test_smooth_against_library_and_invariants():
+    rng = np.random.default_rng(31)
+    c = rng.standard_normal((9, 10, 12)).astype(np.float32)
+    for w in (oracle.box_weights((3, 5, 1)), oracle.gauss_weights((3.0, 2.0, 1.0)),
+              oracle.gauss_weights((4.0, 2.0, 3.0), (20.0, -35.0, 60.0))):
+        assert np.allclose(oracle.smooth(c, w), smooth_library(c, w), rtol=0, atol=1e-13)
+    # constants stay constant (renormalised at the faces)
+    k = np.full((5, 6, 7), 2.5, dtype=np.float32)
+    assert np.allclose(oracle.smooth(k, oracle.gauss_weights((3.0, 3.0, 3.0), (10, 20, 30))),
+                       2.5, rtol=0, atol=1e-14)
+    # a symmetric kernel commutes with flipping the cube
+    w = oracle.gauss_weights((3.0, 2.0, 2.0))
+    assert np.allclose(oracle.smooth(c[:, :, ::-1], w), oracle.smooth(c, w)[:, :, ::-1],
+                       rtol=0, atol=1e-13)
