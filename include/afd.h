@@ -273,6 +273,29 @@ afd_status afd_sum(afd_ctx *ctx, const float *cube, int64_t n, double *out);
  * expired (the error word is then cleared). */
 afd_status afd_sync(afd_ctx *ctx);
 
+/* The box (mean) filter of Sec. 3.1: out(p) = the mean of the voxels of the
+ * N[0] x N[1] x N[2] window centred on p that lie inside the cube (the
+ * boundary rule is this library's reading: the paper states none; constants
+ * stay constant).  N odd, N[0], N[1] <= 49, N[2] <= 25.  in, out: DEVICE
+ * float32 cubes, distinct and not overlapping.  One fused pass on the
+ * context's stream; asynchronous. */
+afd_status afd_smooth_box(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
+                          int64_t nz, const int *N);
+
+/* The Gaussian filter of Sec. 3.2: a normalised correlation (as
+ * afd_smooth_box) with G = exp(-sum_i x_i^2 / (2 sigma_i^2)),
+ * sigma_i = fwhm[i] / (2 sqrt(2 ln 2)), rotated by R = Rz Ry Rx (angles_deg
+ * = {theta_x, theta_y, theta_z} in degrees; K(p) = G(R^T p)), truncated
+ * where the kernel's ellipsoid passes `truncate` sigma along each axis
+ * (radius ceil(truncate sqrt(Sigma_aa)), Sigma = R diag(sigma^2) R^T;
+ * truncate 0 = 3).  angles_deg NULL or all zero: the separable fused pass
+ * (radius <= 24 in x and y, <= 12 in z); otherwise a direct 3-D correlation
+ * whose weights and plane ring must fit in shared memory (AFD_EINVAL if
+ * not), preceded by a synchronous upload of the weights. */
+afd_status afd_smooth_gauss(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
+                            int64_t nz, const float *fwhm, const float *angles_deg,
+                            float truncate);
+
 /* The paper's smoothing-quality diagnostic F (Sec. 4, eqs. "F_equa",
  * "Sequa", "Mfequa") and recovered-signal fraction F_M (Sec. 5, eq.
  * "sums_equa") of a filtered cube against its original, over a ROI box.

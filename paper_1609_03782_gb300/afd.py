@@ -52,6 +52,8 @@ def _load():
         "afd_filter_rel": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int, vp], c_int),
         "afd_f_diagnostic": ([vp, vp, vp, vp, i64, i64, i64, vp, ctypes.c_double,
                               ctypes.c_double, ctypes.c_double, ctypes.c_double, vp], c_int),
+        "afd_smooth_box": ([vp, vp, vp, i64, i64, i64, vp], c_int),
+        "afd_smooth_gauss": ([vp, vp, vp, i64, i64, i64, vp, vp, f32], c_int),
         "afd_pass_timing": ([vp, c_int], c_int),
         "afd_pass_timing_read": ([vp, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int64)], c_int),
@@ -263,6 +265,39 @@ def afd_filter_rel(ctx: Context, cube_in: torch.Tensor, cube_out: torch.Tensor, 
     _check(_lib.afd_filter_rel(ctx.handle, p_in, p_out, nx, ny, nz, _spacing(spacing),
                                float(k_rms), float(dt), int(n_iter), COND[conductance], kp),
            "afd_filter_rel", ctx)
+    return cube_out
+
+
+def _smooth_args(cube_in: torch.Tensor, cube_out: torch.Tensor):
+    for t in (cube_in, cube_out):
+        if not t.is_cuda or t.dtype != torch.float32:
+            raise ValueError("CUDA float32 cubes expected")
+    if cube_in.shape != cube_out.shape:
+        raise ValueError("input and output shapes differ")
+    p_in, nx, ny, nz = _cube_args(cube_in)
+    p_out, _, _, _ = _cube_args(cube_out)
+    return p_in, p_out, nx, ny, nz
+
+
+def afd_smooth_box(ctx: Context, cube_in: torch.Tensor, cube_out: torch.Tensor, N) -> torch.Tensor:
+    """Box (mean) filter of odd window N = (N_x, N_y, N_z) (Sec. 3.1)."""
+    p_in, p_out, nx, ny, nz = _smooth_args(cube_in, cube_out)
+    n = (ctypes.c_int * 3)(*[int(v) for v in N])
+    _use_current_stream(ctx, cube_in)
+    _check(_lib.afd_smooth_box(ctx.handle, p_in, p_out, nx, ny, nz, n), "afd_smooth_box", ctx)
+    return cube_out
+
+
+def afd_smooth_gauss(ctx: Context, cube_in: torch.Tensor, cube_out: torch.Tensor, fwhm,
+                     angles_deg=None, truncate: float = 0.0) -> torch.Tensor:
+    """Gaussian filter (Sec. 3.2): FWHM per axis, optional Euler rotation
+    (degrees), truncation in sigma (0 = 3)."""
+    p_in, p_out, nx, ny, nz = _smooth_args(cube_in, cube_out)
+    f = (ctypes.c_float * 3)(*[float(v) for v in fwhm])
+    a = None if angles_deg is None else (ctypes.c_float * 3)(*[float(v) for v in angles_deg])
+    _use_current_stream(ctx, cube_in)
+    _check(_lib.afd_smooth_gauss(ctx.handle, p_in, p_out, nx, ny, nz, f, a, float(truncate)),
+           "afd_smooth_gauss", ctx)
     return cube_out
 
 

@@ -5,6 +5,8 @@
 // iteration driver.  Every step of the filter runs in the CUDA kernels of
 // this directory.
 #include <cmath>
+#include <algorithm>
+#include <vector>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -706,6 +708,166 @@ afd_status afd_f_diagnostic(afd_ctx *ctx, const float *orig, const float *filt,
     r.F_M = (model && r.S_m != 0.0) ? std::fabs(r.S_mf) / std::fabs(r.S_m) : nan;
     *out = r;
     return AFD_OK;
+}
+
+namespace {
+bool cubes_disjoint(const float *a, const float *b, int64_t n)
+{
+    const char *pa = reinterpret_cast<const char *>(a);
+    const char *pb = reinterpret_cast<const char *>(b);
+    const size_t bytes = static_cast<size_t>(n) * sizeof(float);
+    return !(pa < pb + bytes && pb < pa + bytes);
+}
+
+constexpr double kFwhmPerSigma = 2.3548200450309493;  // 2 sqrt(2 ln 2)
+
+// R = Rz(az) Ry(ay) Rx(ax), angles in degrees, row-major.
+void euler_rotation(const float *deg, double R[3][3])
+{
+    const double d2r = 3.14159265358979323846 / 180.0;
+    const double ax = deg[0] * d2r, ay = deg[1] * d2r, az = deg[2] * d2r;
+    const double cx = std::cos(ax), sx = std::sin(ax), cy = std::cos(ay), sy = std::sin(ay);
+    const double cz = std::cos(az), sz = std::sin(az);
+    const double Rx[3][3] = {{1, 0, 0}, {0, cx, -sx}, {0, sx, cx}};
+    const double Ry[3][3] = {{cy, 0, sy}, {0, 1, 0}, {-sy, 0, cy}};
+    const double Rz[3][3] = {{cz, -sz, 0}, {sz, cz, 0}, {0, 0, 1}};
+    double T[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            T[i][j] = 0.0;
+            for (int k = 0; k < 3; ++k)
+                T[i][j] += Ry[i][k] * Rx[k][j];
+        }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            R[i][j] = 0.0;
+            for (int k = 0; k < 3; ++k)
+                R[i][j] += Rz[i][k] * T[k][j];
+        }
+}
+}  // namespace
+
+afd_status afd_smooth_box(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
+                          int64_t nz, const int *N)
+{
+    if (!ctx || !in || !out || !N || !dims_ok(nx, ny, nz) || !cubes_disjoint(in, out, nx * ny * nz))
+        return AFD_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (N[a] < 1 || N[a] % 2 == 0)
+            return AFD_EINVAL;
+    afd::SepWeights w;
+    w.rx = N[0] / 2;
+    w.ry = N[1] / 2;
+    w.rz = N[2] / 2;
+    if (w.rx > afd::kSepMaxR || w.ry > afd::kSepMaxR || w.rz > afd::kSepMaxRz)
+        return AFD_EINVAL;
+    for (int k = 0; k < 2 * afd::kSepMaxR + 1; ++k)
+        w.wx[k] = w.wy[k] = 1.0f;
+    for (int k = 0; k < 2 * afd::kSepMaxRz + 1; ++k)
+        w.wz[k] = 1.0f;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    cudaError_t e = afd::launch_smooth_sep(in, out, static_cast<int>(nx), static_cast<int>(ny),
+                                           static_cast<int>(nz), w, ctx->stream);
+    ctx->launches++;
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+}
+
+afd_status afd_smooth_gauss(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
+                            int64_t nz, const float *fwhm, const float *angles_deg,
+                            float truncate)
+{
+    if (!ctx || !in || !out || !fwhm || !dims_ok(nx, ny, nz) ||
+        !cubes_disjoint(in, out, nx * ny * nz))
+        return AFD_EINVAL;
+    if (truncate == 0.0f)
+        truncate = 3.0f;
+    if (!(truncate > 0.0f) || !std::isfinite(truncate))
+        return AFD_EINVAL;
+    double sig[3];
+    for (int a = 0; a < 3; ++a) {
+        if (!(fwhm[a] > 0.0f) || !std::isfinite(fwhm[a]))
+            return AFD_EINVAL;
+        sig[a] = static_cast<double>(fwhm[a]) / kFwhmPerSigma;
+    }
+    bool rotated = false;
+    if (angles_deg)
+        for (int a = 0; a < 3; ++a) {
+            if (!std::isfinite(angles_deg[a]))
+                return AFD_EINVAL;
+            rotated = rotated || angles_deg[a] != 0.0f;
+        }
+    const double t = static_cast<double>(truncate);
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    const int inx = static_cast<int>(nx), iny = static_cast<int>(ny), inz = static_cast<int>(nz);
+    cudaError_t e;
+    if (!rotated) {
+        afd::SepWeights w;
+        int r[3];
+        for (int a = 0; a < 3; ++a)
+            r[a] = static_cast<int>(std::ceil(t * sig[a] - 1e-12));
+        if (r[0] > afd::kSepMaxR || r[1] > afd::kSepMaxR || r[2] > afd::kSepMaxRz)
+            return AFD_EINVAL;
+        w.rx = r[0];
+        w.ry = r[1];
+        w.rz = r[2];
+        float *dst[3] = {w.wx, w.wy, w.wz};
+        for (int a = 0; a < 3; ++a)
+            for (int k = 0; k <= 2 * r[a]; ++k) {
+                const double u = (k - r[a]) / sig[a];
+                dst[a][k] = static_cast<float>(std::exp(-0.5 * u * u));
+            }
+        e = afd::launch_smooth_sep(in, out, inx, iny, inz, w, ctx->stream);
+    } else {
+        // K(p) = G(R^T p); extent of the ellipsoid along axis a:
+        // sqrt(Sigma_aa), Sigma = R diag(sigma^2) R^T
+        double R[3][3];
+        euler_rotation(angles_deg, R);
+        int r[3];
+        for (int a = 0; a < 3; ++a) {
+            double caa = 0.0;
+            for (int b = 0; b < 3; ++b)
+                caa += R[a][b] * R[a][b] * sig[b] * sig[b];
+            r[a] = static_cast<int>(std::ceil(t * std::sqrt(caa) - 1e-12));
+        }
+        if (r[0] > 64 || r[1] > 64 || r[2] > 64 ||
+            afd::smooth_direct_smem(r[0], r[1], r[2]) > 227 * 1024)
+            return AFD_EINVAL;  // too large for the shared-memory ring
+        const int WX = 2 * r[0] + 1, WY = 2 * r[1] + 1, WZ = 2 * r[2] + 1;
+        std::vector<float> W(static_cast<size_t>(WX) * WY * WZ);
+        for (int dz = -r[2]; dz <= r[2]; ++dz)
+            for (int dy = -r[1]; dy <= r[1]; ++dy)
+                for (int dx = -r[0]; dx <= r[0]; ++dx) {
+                    const double p[3] = {static_cast<double>(dx), static_cast<double>(dy),
+                                         static_cast<double>(dz)};
+                    double q = 0.0;
+                    for (int i = 0; i < 3; ++i) {
+                        const double u = (R[0][i] * p[0] + R[1][i] * p[1] + R[2][i] * p[2]) /
+                                         sig[i];  // (R^T p)_i / sigma_i
+                        q += u * u;
+                    }
+                    W[(dx + r[0]) + WX * ((dy + r[1]) + WY * (dz + r[2]))] =
+                        static_cast<float>(std::exp(-0.5 * q));
+                }
+        st = ensure_buffer(ctx, &ctx->fd_buf, &ctx->fd_bytes,
+                           std::max(ctx->fd_bytes, W.size() * sizeof(float)));
+        if (st != AFD_OK)
+            return st;
+        // the weights share the diagnostic's scratch: stream-ordered, copied
+        // from host memory before the kernel that reads them
+        e = cudaMemcpyAsync(ctx->fd_buf, W.data(), W.size() * sizeof(float),
+                            cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(ctx->stream);  // W is a local buffer
+        if (e == cudaSuccess)
+            e = afd::launch_smooth_direct(in, out, inx, iny, inz, ctx->fd_buf, r[0], r[1], r[2],
+                                          ctx->stream);
+    }
+    ctx->launches++;
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
 }
 
 afd_status afd_filter_intensity(afd_ctx *ctx, const float *in, float *out, int64_t nx,

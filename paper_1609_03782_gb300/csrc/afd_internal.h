@@ -146,6 +146,20 @@ cudaError_t launch_dequantize(int S, const void *in, float *out, int64_t n, floa
 // ---- FP64 statistics -------------------------------------------------------
 constexpr int kStatsThreads = 256;
 // partials: 4 doubles per block; out4: sum, sum sq, negative sum sq, count
+// Box / Gaussian smoothing (normalised correlation).  Separable weights:
+// wx[0..2rx], wy[0..2ry], wz[0..2rz] (offset k - r).
+constexpr int kSepMaxR = 24;   // x and y radius of the separable kernel
+constexpr int kSepMaxRz = 12;  // z radius (a template parameter)
+struct SepWeights {
+    float wx[2 * kSepMaxR + 1], wy[2 * kSepMaxR + 1], wz[2 * kSepMaxRz + 1];
+    int rx, ry, rz;
+};
+cudaError_t launch_smooth_sep(const float *in, float *out, int nx, int ny, int nz,
+                              const SepWeights &w, cudaStream_t stream);
+// Direct correlation with W (device, x fastest) of (2rx+1)(2ry+1)(2rz+1).
+cudaError_t launch_smooth_direct(const float *in, float *out, int nx, int ny, int nz,
+                                 const float *W, int rx, int ry, int rz, cudaStream_t stream);
+size_t smooth_direct_smem(int rx, int ry, int rz);  // bytes of shared memory it needs
 // F diagnostic sums over the ROI box roi = {x0, x1, y0, y1, z0, z1} of cubes
 // with row pitch nx and ny rows per plane: out6 = {S_of, S_oo, S_mf, S_m, N_o,
 // N_f} (device doubles; im may be null).  t_o, t_f: float thresholds already
