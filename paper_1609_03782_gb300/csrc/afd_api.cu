@@ -747,6 +747,30 @@ void euler_rotation(const float *deg, double R[3][3])
 }
 }  // namespace
 
+namespace {
+// The separable smoothing pass: TMA-streamed when the rows are a multiple of
+// 16 bytes and both cubes 16-byte aligned, else the plain-load kernel (both
+// give the same floats).
+afd_status smooth_separable(afd_ctx *ctx, const float *in, float *out, int nx, int ny, int nz,
+                            const afd::SepWeights &w)
+{
+    cudaError_t e;
+    if (stream_kernel_fits(in, out, nx)) {
+        int bw = 0, bh = 0, hx = 0;
+        afd::smooth_tma_box(w.rx, w.ry, &bw, &bh, &hx);
+        CUtensorMap map;
+        afd_status st = encode_box_map(ctx, &map, in, afd::STORE_F32, bw, bh, nx, ny, nz);
+        if (st != AFD_OK)
+            return st;
+        e = afd::launch_smooth_sep_tma(map, out, nx, ny, nz, w, hx, ctx->d_err, ctx->stream);
+    } else {
+        e = afd::launch_smooth_sep(in, out, nx, ny, nz, w, ctx->stream);
+    }
+    ctx->launches++;
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+}
+}  // namespace
+
 afd_status afd_smooth_box(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
                           int64_t nz, const int *N)
 {
@@ -768,10 +792,8 @@ afd_status afd_smooth_box(afd_ctx *ctx, const float *in, float *out, int64_t nx,
     afd_status st = set_device(ctx);
     if (st != AFD_OK)
         return st;
-    cudaError_t e = afd::launch_smooth_sep(in, out, static_cast<int>(nx), static_cast<int>(ny),
-                                           static_cast<int>(nz), w, ctx->stream);
-    ctx->launches++;
-    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+    return smooth_separable(ctx, in, out, static_cast<int>(nx), static_cast<int>(ny),
+                            static_cast<int>(nz), w);
 }
 
 afd_status afd_smooth_gauss(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
@@ -820,7 +842,7 @@ afd_status afd_smooth_gauss(afd_ctx *ctx, const float *in, float *out, int64_t n
                 const double u = (k - r[a]) / sig[a];
                 dst[a][k] = static_cast<float>(std::exp(-0.5 * u * u));
             }
-        e = afd::launch_smooth_sep(in, out, inx, iny, inz, w, ctx->stream);
+        return smooth_separable(ctx, in, out, inx, iny, inz, w);
     } else {
         // K(p) = G(R^T p); extent of the ellipsoid along axis a:
         // sqrt(Sigma_aa), Sigma = R diag(sigma^2) R^T
@@ -838,6 +860,7 @@ afd_status afd_smooth_gauss(afd_ctx *ctx, const float *in, float *out, int64_t n
             return AFD_EINVAL;  // too large for the shared-memory ring
         const int WX = 2 * r[0] + 1, WY = 2 * r[1] + 1, WZ = 2 * r[2] + 1;
         std::vector<float> W(static_cast<size_t>(WX) * WY * WZ);
+        double wsum = 0.0;
         for (int dz = -r[2]; dz <= r[2]; ++dz)
             for (int dy = -r[1]; dy <= r[1]; ++dy)
                 for (int dx = -r[0]; dx <= r[0]; ++dx) {
@@ -849,8 +872,9 @@ afd_status afd_smooth_gauss(afd_ctx *ctx, const float *in, float *out, int64_t n
                                          sig[i];  // (R^T p)_i / sigma_i
                         q += u * u;
                     }
-                    W[(dx + r[0]) + WX * ((dy + r[1]) + WY * (dz + r[2]))] =
-                        static_cast<float>(std::exp(-0.5 * q));
+                    const float wq = static_cast<float>(std::exp(-0.5 * q));
+                    W[(dx + r[0]) + WX * ((dy + r[1]) + WY * (dz + r[2]))] = wq;
+                    wsum += static_cast<double>(wq);
                 }
         st = ensure_buffer(ctx, &ctx->fd_buf, &ctx->fd_bytes,
                            std::max(ctx->fd_bytes, W.size() * sizeof(float)));
@@ -864,7 +888,7 @@ afd_status afd_smooth_gauss(afd_ctx *ctx, const float *in, float *out, int64_t n
             e = cudaStreamSynchronize(ctx->stream);  // W is a local buffer
         if (e == cudaSuccess)
             e = afd::launch_smooth_direct(in, out, inx, iny, inz, ctx->fd_buf, r[0], r[1], r[2],
-                                          ctx->stream);
+                                          static_cast<float>(wsum), ctx->stream);
     }
     ctx->launches++;
     return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);

@@ -157,9 +157,18 @@ struct SepWeights {
 cudaError_t launch_smooth_sep(const float *in, float *out, int nx, int ny, int nz,
                               const SepWeights &w, cudaStream_t stream);
 // Direct correlation with W (device, x fastest) of (2rx+1)(2ry+1)(2rz+1).
+// wsum: the total weight (the divisor of voxels whose window is inside).
 cudaError_t launch_smooth_direct(const float *in, float *out, int nx, int ny, int nz,
-                                 const float *W, int rx, int ry, int rz, cudaStream_t stream);
+                                 const float *W, int rx, int ry, int rz, float wsum,
+                                 cudaStream_t stream);
 size_t smooth_direct_smem(int rx, int ry, int rz);  // bytes of shared memory it needs
+// The separable pass with TMA-streamed planes: nx % 4 == 0, 16-byte aligned
+// cubes.  tmap: 3-D float32 map over the input with the box of
+// smooth_tma_box (x halo hx, a multiple of 4 >= rx).
+void smooth_tma_box(int rx, int ry, int *box_w, int *box_h, int *hx);
+size_t smooth_tma_smem(int ry, int hx);
+cudaError_t launch_smooth_sep_tma(const CUtensorMap &tmap, float *out, int nx, int ny, int nz,
+                                  const SepWeights &w, int hx, int *err, cudaStream_t stream);
 // F diagnostic sums over the ROI box roi = {x0, x1, y0, y1, z0, z1} of cubes
 // with row pitch nx and ny rows per plane: out6 = {S_of, S_oo, S_mf, S_m, N_o,
 // N_f} (device doubles; im may be null).  t_o, t_f: float thresholds already

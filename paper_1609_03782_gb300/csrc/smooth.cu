@@ -20,6 +20,7 @@
 #include <cmath>
 
 #include "afd_internal.h"
+#include "afd_ptx.cuh"
 
 namespace afd {
 namespace {
@@ -166,17 +167,198 @@ __global__ void __launch_bounds__(kSmThreads)
     }
 }
 
+// The separable pass with its planes streamed by TMA (rows of a multiple of
+// 16 bytes): warp 8 issues one 3-D load per plane (tile + halo, zero outside
+// the cube) into a ring of kSmSlots slots.  Warps 0-7 convolve the slot's
+// rows along x into a double-buffered shared-memory plane, release the slot,
+// meet at one named barrier, convolve along y and keep the z window in
+// registers: the same products and sums, in the same order, as smooth_sep.
+// Every mbarrier wait is bounded (kWaitLimitNs); a thread whose wait expires
+// records the error and keeps stepping without waiting again, so every
+// consumer reaches every named barrier and the CTA ends.
+constexpr int kSmSlots = 4;
+constexpr int kSmTmaThreads = kSmThreads + 32;
+
+__device__ __forceinline__ void consumer_barrier()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(kSmThreads) : "memory");
+}
+
+template <int RZ>
+__global__ void __launch_bounds__(kSmTmaThreads)
+    smooth_sep_tma(const __grid_constant__ CUtensorMap tmap, float *__restrict__ out, int nx,
+                   int ny, int nz, int tiles_x, int tiles_y, int zc, int hx,
+                   const __grid_constant__ SepWeights w, int *err)
+{
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t base = smem_u32(smem_raw);
+    unsigned char *smem = smem_raw + ((128u - (base & 127u)) & 127u);
+    const int rx = w.rx, ry = w.ry;
+    const int SW = SX + 2 * hx, SH = SY + 2 * ry;  // slot: SH rows of SW floats
+    const uint32_t slot_bytes = static_cast<uint32_t>(SW * SH) * 4u;
+    const uint32_t slot_stride = (slot_bytes + 127u) & ~127u;
+    float *X = reinterpret_cast<float *>(smem + kSmSlots * slot_stride);  // 2 x SH x SX
+    uint64_t *full = reinterpret_cast<uint64_t *>(X + 2 * SH * SX);
+    uint64_t *empty = full + kSmSlots;
+
+    int t = blockIdx.x;
+    const int bx = t % tiles_x;
+    t /= tiles_x;
+    const int by = t % tiles_y;
+    const int bz = t / tiles_y;
+    const int x0 = bx * SX, y0 = by * SY;
+    const int zs = bz * zc, ze = min(zs + zc, nz);
+    const int zlo = max(zs - RZ, 0), zhi = min(ze + RZ, nz) - 1;  // planes loaded
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int i = 0; i < kSmSlots; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kSmThreads / 32);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == kSmThreads / 32) {  // ---- producer
+        if (lane == 0) {
+            for (int j = 0; j <= zhi - zlo; ++j) {
+                const int slot = j % kSmSlots, use = j / kSmSlots;
+                if (use > 0 && !mbar_wait(&empty[slot], (use - 1) & 1u, err, kErrWaitEmpty))
+                    return;
+                mbar_arrive_expect_tx(&full[slot], slot_bytes);
+                tma_load_3d(smem + slot * slot_stride, &tmap, x0 - hx, y0 - ry, zlo + j,
+                            &full[slot]);
+            }
+        }
+        return;
+    }
+
+    // ---- consumers: thread (qx, ty) owns 4 voxels of row ty
+    const int qx = tid & 15, ty = tid >> 4;
+    const int xq = x0 + 4 * qx, yr = y0 + ty;
+    float den_xy[4];
+    {
+        float dy = 0.0f;
+        for (int k = 0; k <= 2 * ry; ++k) {
+            const int q = yr + k - ry;
+            if (q >= 0 && q < ny)
+                dy = __fadd_rn(dy, w.wy[k]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float dx = 0.0f;
+            for (int k = 0; k <= 2 * rx; ++k) {
+                const int q = xq + j + k - rx;
+                if (q >= 0 && q < nx)
+                    dx = __fadd_rn(dx, w.wx[k]);
+            }
+            den_xy[j] = __fmul_rn(dx, dy);
+        }
+    }
+    float ring[2 * RZ + 1][4];
+#pragma unroll
+    for (int m = 0; m < 2 * RZ + 1; ++m)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            ring[m][j] = 0.0f;
+
+    bool waiting = true;  // false after an expired wait: no more waits
+    for (int zi = zs - RZ; zi < ze + RZ; ++zi) {
+        const bool have = zi >= zlo && zi <= zhi;  // the same for the whole CTA
+        float *Xb = X + (zi & 1) * SH * SX;
+        if (have) {
+            const int j = zi - zlo, slot = j % kSmSlots;
+            if (waiting && !mbar_wait(&full[slot], (j / kSmSlots) & 1u, err, kErrWaitFull))
+                waiting = false;
+            const float *S = reinterpret_cast<const float *>(smem + slot * slot_stride);
+            // x sums of every slot row: 4 outputs per task; the window of
+            // output column 4q starts at column hx + 4q - rx >= 0 and the last
+            // read is column hx + 4q + rx + 3 <= SW - 1 (hx >= rx)
+            for (int task = tid; task < SH * 16; task += kSmThreads) {
+                const int r = task >> 4, q = task & 15;
+                const float *row = S + r * SW + hx + 4 * q - rx;
+                float v0 = row[0], v1 = row[1], v2 = row[2];
+                float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+                for (int k = 0; k <= 2 * rx; ++k) {
+                    const float v3 = row[k + 3];
+                    const float wk = w.wx[k];
+                    a0 = __fmaf_rn(wk, v0, a0);
+                    a1 = __fmaf_rn(wk, v1, a1);
+                    a2 = __fmaf_rn(wk, v2, a2);
+                    a3 = __fmaf_rn(wk, v3, a3);
+                    v0 = v1;
+                    v1 = v2;
+                    v2 = v3;
+                }
+                *reinterpret_cast<float4 *>(Xb + r * SX + 4 * q) = make_float4(a0, a1, a2, a3);
+            }
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&empty[slot]);
+        }
+        // Xb is complete; the other buffer, written next plane, was last read
+        // before this barrier
+        consumer_barrier();
+        float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (have) {
+            for (int k = 0; k <= 2 * ry; ++k) {
+                const float wk = w.wy[k];
+                const float4 v = *reinterpret_cast<const float4 *>(Xb + (ty + k) * SX + 4 * qx);
+                c[0] = __fmaf_rn(wk, v.x, c[0]);
+                c[1] = __fmaf_rn(wk, v.y, c[1]);
+                c[2] = __fmaf_rn(wk, v.z, c[2]);
+                c[3] = __fmaf_rn(wk, v.w, c[3]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 2 * RZ; ++m)
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+                ring[m][jj] = ring[m + 1][jj];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+            ring[2 * RZ][jj] = c[jj];
+        const int zo = zi - RZ;
+        if (zo >= zs && yr < ny && xq < nx) {
+            float dz = 0.0f;
+#pragma unroll
+            for (int k = 0; k <= 2 * RZ; ++k) {
+                const int q = zo + k - RZ;
+                if (q >= 0 && q < nz)
+                    dz = __fadd_rn(dz, w.wz[k]);
+            }
+            float o[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                float sum = 0.0f;
+#pragma unroll
+                for (int k = 0; k <= 2 * RZ; ++k)
+                    sum = __fmaf_rn(w.wz[k], ring[k][jj], sum);
+                o[jj] = __fdiv_rn(sum, __fmul_rn(den_xy[jj], dz));
+            }
+            // nx % 4 == 0 and xq % 4 == 0: the quad is inside the row
+            *reinterpret_cast<float4 *>(out + (static_cast<int64_t>(zo) * ny + yr) * nx + xq) =
+                make_float4(o[0], o[1], o[2], o[3]);
+        }
+    }
+}
+
 // Direct correlation with a full (2rx+1) x (2ry+1) x (2rz+1) weight array
 // (rotated Gaussian).  Shared memory: the weights, then a ring of 2 rz + 1
-// raw planes of PH x PW (tile + halo).
+// raw planes of PH x PW (tile + halo).  A voxel whose window lies inside the
+// cube divides by the kernel's total weight wsum (summed in double on the
+// host, rounded once); one within a radius of a face sums the weights of its
+// in-cube taps.
 __global__ void __launch_bounds__(kSmThreads)
     smooth_direct(const float *__restrict__ in, float *__restrict__ out, int nx, int ny, int nz,
                   int tiles_x, int tiles_y, int zc, const float *__restrict__ W, int rx, int ry,
-                  int rz)
+                  int rz, float wsum)
 {
     extern __shared__ float sm[];
     const int WX = 2 * rx + 1, WY = 2 * ry + 1, WZ = 2 * rz + 1;
-    const int PW = SX + 2 * rx + 4;  // + 4: the sliding window reads 4 past its last tap
+    const int PW = SX + 2 * rx + 4;  // + 4: room for the sliding window's reads
     const int PH = SY + 2 * ry;
     float *Ws = sm;
     float *ring = sm + WX * WY * WZ;
@@ -193,15 +375,15 @@ __global__ void __launch_bounds__(kSmThreads)
     const int warp = tid >> 5, lane = tid & 31;
     const int qx = tid & 15, ty = tid >> 4;
     const int xq = x0 + 4 * qx, yr = y0 + ty;
+    const bool xy_inside = xq - rx >= 0 && xq + 3 + rx < nx && yr - ry >= 0 && yr + ry < ny;
 
     for (int i = tid; i < WX * WY * WZ; i += kSmThreads)
         Ws[i] = W[i];
 
-    // normalisation: the in-cube weight of each output voxel depends on z;
-    // it is summed with the same loops as the numerator, from a ones plane
     for (int zi = zs - rz; zi < ze + rz; ++zi) {
-        // ---- load plane zi into its ring slot (the slot last read for the
-        // output plane zi - 2 rz - 1, finished before the barrier below)
+        // ---- load plane zi into its ring slot (the slot's previous plane,
+        // zi - 2 rz - 1, was last read before the barrier ending the
+        // previous iteration)
         float *P = ring + ((zi - (zs - rz)) % WZ) * PH * PW;
         const bool zin = zi >= 0 && zi < nz;
         const float *src = in + static_cast<int64_t>(zi) * nx * ny;
@@ -218,34 +400,51 @@ __global__ void __launch_bounds__(kSmThreads)
         __syncthreads();
         const int zo = zi - rz;  // every plane of its window is now in the ring
         if (zo >= zs && yr < ny) {
-            float a[4] = {0.0f, 0.0f, 0.0f, 0.0f}, d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             for (int dz = 0; dz < WZ; ++dz) {
                 const int qz = zo - rz + dz;
                 if (qz < 0 || qz >= nz)
-                    continue;
+                    continue;  // zero plane
                 const float *Pz = ring + ((qz - (zs - rz)) % WZ) * PH * PW;
                 for (int dy = 0; dy < WY; ++dy) {
-                    const int qy = yr - ry + dy;
-                    if (qy < 0 || qy >= ny)
-                        continue;
+                    // row ty + dy of the slot; the window's last read is
+                    // column 4 qx + 2 rx + 3 < PW
                     const float *row = Pz + (ty + dy) * PW + 4 * qx;
                     const float *wrow = Ws + (dz * WY + dy) * WX;
-                    float v0 = row[0], v1 = row[1], v2 = row[2], v3 = row[3];
+                    float v0 = row[0], v1 = row[1], v2 = row[2];
                     for (int dx = 0; dx < WX; ++dx) {
+                        const float v3 = row[dx + 3];
                         const float wk = wrow[dx];
-                        const int gx = xq - rx + dx;
                         a[0] = __fmaf_rn(wk, v0, a[0]);
                         a[1] = __fmaf_rn(wk, v1, a[1]);
                         a[2] = __fmaf_rn(wk, v2, a[2]);
                         a[3] = __fmaf_rn(wk, v3, a[3]);
-                        d[0] = (gx >= 0 && gx < nx) ? __fadd_rn(d[0], wk) : d[0];
-                        d[1] = (gx + 1 >= 0 && gx + 1 < nx) ? __fadd_rn(d[1], wk) : d[1];
-                        d[2] = (gx + 2 >= 0 && gx + 2 < nx) ? __fadd_rn(d[2], wk) : d[2];
-                        d[3] = (gx + 3 >= 0 && gx + 3 < nx) ? __fadd_rn(d[3], wk) : d[3];
                         v0 = v1;
                         v1 = v2;
                         v2 = v3;
-                        v3 = row[dx + 4];
+                    }
+                }
+            }
+            float d[4] = {wsum, wsum, wsum, wsum};
+            if (!(xy_inside && zo - rz >= 0 && zo + rz < nz)) {
+                // near a face: the weight of the in-cube taps only
+                d[0] = d[1] = d[2] = d[3] = 0.0f;
+                for (int dz = 0; dz < WZ; ++dz) {
+                    const int qz = zo - rz + dz;
+                    if (qz < 0 || qz >= nz)
+                        continue;
+                    for (int dy = 0; dy < WY; ++dy) {
+                        const int qy = yr - ry + dy;
+                        if (qy < 0 || qy >= ny)
+                            continue;
+                        const float *wrow = Ws + (dz * WY + dy) * WX;
+                        for (int dx = 0; dx < WX; ++dx) {
+                            const int gx = xq - rx + dx;
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                if (gx + j >= 0 && gx + j < nx)
+                                    d[j] = __fadd_rn(d[j], wrow[dx]);
+                        }
                     }
                 }
             }
@@ -276,6 +475,45 @@ cudaError_t sep_launch(const float *in, float *out, int nx, int ny, int nz, cons
     return cudaGetLastError();
 }
 
+template <int RZ>
+cudaError_t sep_tma_launch(const CUtensorMap &tmap, float *out, int nx, int ny, int nz,
+                           const SepWeights &w, int hx, int *err, cudaStream_t stream)
+{
+    const int tiles_x = (nx + SX - 1) / SX, tiles_y = (ny + SY - 1) / SY;
+    const int zc = nz < 64 ? nz : 64;
+    const int tiles_z = (nz + zc - 1) / zc;
+    const size_t smem = smooth_tma_smem(w.ry, hx);
+    cudaError_t e = cudaFuncSetAttribute(smooth_sep_tma<RZ>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess)
+        return e;
+    smooth_sep_tma<RZ><<<tiles_x * tiles_y * tiles_z, kSmTmaThreads, smem, stream>>>(
+        tmap, out, nx, ny, nz, tiles_x, tiles_y, zc, hx, w, err);
+    return cudaGetLastError();
+}
+
+template <int... R>
+struct SepTmaTable;
+template <>
+struct SepTmaTable<> {
+    static cudaError_t run(int, const CUtensorMap &, float *, int, int, int, const SepWeights &,
+                           int, int *, cudaStream_t)
+    {
+        return cudaErrorInvalidValue;
+    }
+};
+template <int R0, int... R>
+struct SepTmaTable<R0, R...> {
+    static cudaError_t run(int rz, const CUtensorMap &m, float *out, int nx, int ny, int nz,
+                           const SepWeights &w, int hx, int *err, cudaStream_t s)
+    {
+        if (rz == R0)
+            return sep_tma_launch<R0>(m, out, nx, ny, nz, w, hx, err, s);
+        return SepTmaTable<R...>::run(rz, m, out, nx, ny, nz, w, hx, err, s);
+    }
+};
+
 template <int... R>
 struct SepTable;
 template <>
@@ -299,6 +537,30 @@ struct SepTable<R0, R...> {
 
 }  // namespace
 
+size_t smooth_tma_smem(int ry, int hx)
+{
+    const size_t slot = (static_cast<size_t>(SX + 2 * hx) * (SY + 2 * ry) * 4 + 127) / 128 * 128;
+    const size_t xbuf = 2 * static_cast<size_t>(SY + 2 * ry) * SX * sizeof(float);
+    return kSmSlots * slot + xbuf + 2 * kSmSlots * sizeof(uint64_t) + 128;
+}
+
+void smooth_tma_box(int rx, int ry, int *box_w, int *box_h, int *hx)
+{
+    *hx = (rx + 3) / 4 * 4;  // x halo: >= rx, a multiple of 4 floats (16-byte TMA x)
+    *box_w = SX + 2 * *hx;
+    *box_h = SY + 2 * ry;
+}
+
+cudaError_t launch_smooth_sep_tma(const CUtensorMap &tmap, float *out, int nx, int ny, int nz,
+                                  const SepWeights &w, int hx, int *err, cudaStream_t stream)
+{
+    if (w.rx < 0 || w.rx > kSepMaxR || w.ry < 0 || w.ry > kSepMaxR || w.rz < 0 ||
+        w.rz > kSepMaxRz || hx < w.rx || (nx % 4) != 0)
+        return cudaErrorInvalidValue;
+    return SepTmaTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12>::run(w.rz, tmap, out, nx, ny, nz,
+                                                                     w, hx, err, stream);
+}
+
 size_t smooth_direct_smem(int rx, int ry, int rz)
 {
     const size_t wts = static_cast<size_t>(2 * rx + 1) * (2 * ry + 1) * (2 * rz + 1);
@@ -318,7 +580,8 @@ cudaError_t launch_smooth_sep(const float *in, float *out, int nx, int ny, int n
 }
 
 cudaError_t launch_smooth_direct(const float *in, float *out, int nx, int ny, int nz,
-                                 const float *W, int rx, int ry, int rz, cudaStream_t stream)
+                                 const float *W, int rx, int ry, int rz, float wsum,
+                                 cudaStream_t stream)
 {
     const size_t smem = smooth_direct_smem(rx, ry, rz);
     cudaError_t e = cudaFuncSetAttribute(smooth_direct, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -329,7 +592,7 @@ cudaError_t launch_smooth_direct(const float *in, float *out, int nx, int ny, in
     const int zc = nz < 32 ? nz : 32;
     const int tiles_z = (nz + zc - 1) / zc;
     smooth_direct<<<tiles_x * tiles_y * tiles_z, kSmThreads, smem, stream>>>(
-        in, out, nx, ny, nz, tiles_x, tiles_y, zc, W, rx, ry, rz);
+        in, out, nx, ny, nz, tiles_x, tiles_y, zc, W, rx, ry, rz, wsum);
     return cudaGetLastError();
 }
 

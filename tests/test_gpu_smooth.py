@@ -94,6 +94,25 @@ def test_gauss_rotated_matches_oracle(afd, ctx, shape, fwhm, angles):
     assert_close(got, cube, w, w.size)
 
 
+@pytest.mark.parametrize("shape", [(9, 20, 64), (70, 33, 132), (5, 3, 4)])
+def test_streamed_and_plain_paths_agree(afd, ctx, shape):
+    # nx % 4 == 0 runs the TMA-streamed pass; a sliced (unaligned) view of
+    # the same data runs the plain-load pass: the same floats either way
+    rng = np.random.default_rng(sum(shape))
+    cube = rng.standard_normal(shape).astype(np.float32)
+    d = torch.from_numpy(cube).cuda()
+    big = torch.zeros(cube.size + 1, device="cuda")
+    big[1:] = d.reshape(-1)
+    shifted = big[1:].view(shape)                      # 4-byte offset: not 16-byte aligned
+    for fn, arg in ((afd.afd_smooth_box, (3, 5, 3)), (afd.afd_smooth_gauss, (3.0, 2.0, 4.0))):
+        a = torch.empty_like(d)
+        fn(ctx, d, a, arg)
+        b = torch.empty_like(d)
+        fn(ctx, shifted, b, arg)
+        afd.afd_sync(ctx)
+        assert torch.equal(a, b)
+
+
 def test_constants_and_errors(afd, ctx):
     k = np.full((9, 10, 11), 1.75, dtype=np.float32)
     for got in (gpu_box(afd, ctx, k, (5, 3, 3)), gpu_gauss(afd, ctx, k, (3.0, 4.0, 2.0)),
