@@ -368,6 +368,7 @@ def line_smoothing(afd, ctx):
     benchmark size (512x512x536): one fused separable pass for the box and
     the axis-aligned Gaussian, the direct 3-D correlation for a rotated
     Gaussian.  Algorithmic bytes: 8 per voxel (read + write once)."""
+    import numpy as np
     import torch
     import synth
     cube = synth.galaxy_cube((536, 512, 512), 0, 8, 2)
@@ -383,13 +384,28 @@ def line_smoothing(afd, ctx):
                 lambda: afd.afd_smooth_gauss(ctx, d_in, d_out, (3.0, 3.0, 3.0)),
             "gauss FWHM 3,5,3 rotated 0,0,30 deg (direct 3-D)":
                 lambda: afd.afd_smooth_gauss(ctx, d_in, d_out, (3.0, 5.0, 3.0), (0.0, 0.0, 30.0))}
+    # taps per voxel of the rotated kernel (the direct pass is bound by its
+    # FP32 multiply-adds, not by HBM): radius ceil(3 sqrt(Sigma_aa)) per axis
+    sig = np.array([3.0, 5.0, 3.0]) / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    th = math.radians(30.0)
+    Rz = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1]])
+    cov = Rz @ np.diag(sig ** 2) @ Rz.T
+    taps = int(np.prod([2 * math.ceil(3.0 * math.sqrt(cov[a, a]) - 1e-12) + 1 for a in range(3)]))
+    fma_peak = 152 * 128 * 2.07e9   # FP32 lanes x clock: one FMA per lane per cycle
     rows = []
     for name, fn in runs.items():
         fn()
         ms = _events_ms(fn, 5)
         gbs = 8.0 * n_vox / (ms / 1e3) / 1e9
-        rows.append({"filter": name, "ms": ms, "gvox_s": n_vox / (ms / 1e3) / 1e9,
-                     "algorithmic_GBs": gbs, "frac": gbs / peak})
+        row = {"filter": name, "ms": ms, "gvox_s": n_vox / (ms / 1e3) / 1e9}
+        if "direct" in name:
+            fma_s = taps * n_vox / (ms / 1e3)
+            row.update({"bound": "alu", "taps_per_voxel": taps, "fma_per_s": fma_s,
+                        "peak_fma_per_s": fma_peak, "frac": fma_s / fma_peak,
+                        "peak_note": "152 SMs x 128 FP32 lanes x 2.07 GHz"})
+        else:
+            row.update({"bound": "hbm", "algorithmic_GBs": gbs, "frac": gbs / peak})
+        rows.append(row)
     return {"workload": "512x512x536 float32 synthetic cube (8 disks + 2 tails, seed 0), "
                         "normalised correlation, out of place", "peak_GBs": peak,
             "peak_kind": peak_kind, "rows": rows,
