@@ -613,17 +613,23 @@ def run_afd(args):
         afd.afd_filter_host(ctx, h_in, h_out, K_host, DT, N_ITER, COND)
     te = max_over_ranks(time.perf_counter() - te)
     e2e_sync_value = world * n_vox * N_ITER * args.e2e_steps / te / 1e9
-    # a stream of cubes: each call's copies overlap the previous call's passes
+    # a stream of cubes: each call's copies overlap the previous call's
+    # passes.  Three rounds, the median reported (all listed): the overlap
+    # depends on the host keeping ahead of the GPU, and a shared host can
+    # delay one round.
     for _ in range(2):
         afd.afd_filter_host_async(ctx, h_in, h_out, K_host, DT, N_ITER, COND)
     afd.afd_sync(ctx)
-    barrier()
-    te = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        afd.afd_filter_host_async(ctx, h_in, h_out, K_host, DT, N_ITER, COND)
-    afd.afd_sync(ctx)
-    te = max_over_ranks(time.perf_counter() - te)
-    e2e_value = world * n_vox * N_ITER * args.e2e_steps / te / 1e9
+    e2e_rounds = []
+    for _ in range(3):
+        barrier()
+        te = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            afd.afd_filter_host_async(ctx, h_in, h_out, K_host, DT, N_ITER, COND)
+        afd.afd_sync(ctx)
+        te = max_over_ranks(time.perf_counter() - te)
+        e2e_rounds.append(world * n_vox * N_ITER * args.e2e_steps / te / 1e9)
+    e2e_value = statistics.median(e2e_rounds)
 
     lines = {}
     if rank == 0 and world == 1 and args.lines != "none":
@@ -677,7 +683,8 @@ def run_afd(args):
                     "path": "afd_filter_host_async, one call per step (a stream of cubes): "
                             "pinned host in -> device -> 50 iterations -> pinned host out; "
                             "a call's copies overlap the previous call's passes; afd_sync "
-                            "after the last step",
+                            "after the last step; median of 3 rounds",
+                    "rounds": e2e_rounds,
                     "sync_value": e2e_sync_value,
                     "sync_path": "afd_filter_host (one cube at a time, synchronous: copies "
                                  "and passes in series)"},

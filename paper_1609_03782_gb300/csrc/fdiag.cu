@@ -10,8 +10,9 @@
 // The thresholds arrive as floats already rounded up from nsig x rms (the
 // smallest float >= the exact threshold), so a float comparison takes the
 // same mask decision as the exact one.  Each warp walks rows of the box
-// (lanes along x; float4 loads when the rows are 16-byte aligned, else four
-// scalars per lane per step; all loads issued before they are used); a
+// (lanes along x; four float4 loads per cube per lane per step when the rows
+// are 16-byte aligned, else four scalars; all loads issued before they are
+// used); a
 // lane's four values are summed in float32 and the sums
 // added to float-float (TwoSum) accumulators, converted to double once per
 // thread.  Warps and blocks combine in double in a fixed order, so a result
@@ -83,10 +84,10 @@ __global__ void __launch_bounds__(kFdThreads)
             const float4 *pf = reinterpret_cast<const float4 *>(if_ + base);
             const float4 *pm = MODEL ? reinterpret_cast<const float4 *>(im_ + base) : nullptr;
             const int L4 = L / 4;
-            for (int q = lane; q < L4; q += 64) {
-                float4 vo[2], vf[2], vm[2];
+            for (int q = lane; q < L4; q += 128) {
+                float4 vo[4], vf[4], vm[4];
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
+                for (int k = 0; k < 4; ++k) {
                     const bool in = q + 32 * k < L4;
                     const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                     vo[k] = in ? __ldcs(po + q + 32 * k) : zero;
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(kFdThreads)
                         vm[k] = in ? __ldcs(pm + q + 32 * k) : zero;
                 }
 #pragma unroll
-                for (int k = 0; k < 2; ++k) {
+                for (int k = 0; k < 4; ++k) {
                     const bool in = q + 32 * k < L4;
                     float a_of = 0.0f, a_oo = 0.0f, a_mf = 0.0f, a_m = 0.0f;
                     fd_term<MODEL>(in, vo[k].x, vf[k].x, vm[k].x, t_o, t_f, a_of, a_oo, a_mf, a_m,

@@ -6,7 +6,8 @@
 // Separable kernels (the box, and the Gaussian without rotation):
 // W = wx (x) wy (x) wz, and the in-cube weight factorises into per-axis sums,
 // so out = (wz * (wy * (wx * I))) / (Dx(x) Dy(y) Dz(z)) with zero outside the
-// cube.  One fused pass streams z: a CTA owns a 64 x 16 column of the cube
+// cube, applied as two products with the rounded reciprocals of Dx Dy (per
+// voxel column) and Dz (per plane).  One fused pass streams z: a CTA owns a 64 x 16 column of the cube
 // over a z-chunk; for every input plane it loads the tile and its x/y halo
 // into shared memory (zero outside), convolves along x (a register sliding
 // window per 4 outputs) into a second buffer, then along y, and pushes the
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(kSmThreads)
     const int xq = x0 + 4 * qx, yr = y0 + ty;
 
     // per-axis normalisation of the voxels this thread writes
-    float den_xy[4];  // in-cube weight of x times y
+    float inv_xy[4];
     {
         float dy = 0.0f;
         for (int k = 0; k <= 2 * ry; ++k) {
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(kSmThreads)
                 if (q >= 0 && q < nx)
                     dx = __fadd_rn(dx, w.wx[k]);
             }
-            den_xy[j] = __fmul_rn(dx, dy);
+            inv_xy[j] = __frcp_rn(__fmul_rn(dx, dy));  // 1 / (in-cube weight of x times y)
         }
     }
 
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(kSmThreads)
                 if (q >= 0 && q < nz)
                     dz = __fadd_rn(dz, w.wz[k]);
             }
+            const float inv_z = __frcp_rn(dz);
             float o[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(kSmThreads)
 #pragma unroll
                 for (int k = 0; k <= 2 * RZ; ++k)
                     s = __fmaf_rn(w.wz[k], ring[k][j], s);
-                o[j] = __fdiv_rn(s, __fmul_rn(den_xy[j], dz));
+                o[j] = __fmul_rn(__fmul_rn(s, inv_xy[j]), inv_z);
             }
             float *dst = out + (static_cast<int64_t>(zo) * ny + yr) * nx;
 #pragma unroll
@@ -238,7 +240,7 @@ __global__ void __launch_bounds__(kSmTmaThreads)
     // ---- consumers: thread (qx, ty) owns 4 voxels of row ty
     const int qx = tid & 15, ty = tid >> 4;
     const int xq = x0 + 4 * qx, yr = y0 + ty;
-    float den_xy[4];
+    float inv_xy[4];
     {
         float dy = 0.0f;
         for (int k = 0; k <= 2 * ry; ++k) {
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(kSmTmaThreads)
                 if (q >= 0 && q < nx)
                     dx = __fadd_rn(dx, w.wx[k]);
             }
-            den_xy[j] = __fmul_rn(dx, dy);
+            inv_xy[j] = __frcp_rn(__fmul_rn(dx, dy));  // 1 / (in-cube weight of x times y)
         }
     }
     float ring[2 * RZ + 1][4];
@@ -329,6 +331,7 @@ __global__ void __launch_bounds__(kSmTmaThreads)
                 if (q >= 0 && q < nz)
                     dz = __fadd_rn(dz, w.wz[k]);
             }
+            const float inv_z = __frcp_rn(dz);
             float o[4];
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
@@ -336,7 +339,7 @@ __global__ void __launch_bounds__(kSmTmaThreads)
 #pragma unroll
                 for (int k = 0; k <= 2 * RZ; ++k)
                     sum = __fmaf_rn(w.wz[k], ring[k][jj], sum);
-                o[jj] = __fdiv_rn(sum, __fmul_rn(den_xy[jj], dz));
+                o[jj] = __fmul_rn(__fmul_rn(sum, inv_xy[jj]), inv_z);
             }
             // nx % 4 == 0 and xq % 4 == 0: the quad is inside the row
             *reinterpret_cast<float4 *>(out + (static_cast<int64_t>(zo) * ny + yr) * nx + xq) =
