@@ -328,6 +328,16 @@ afd_status afd_f_diagnostic(afd_ctx *ctx, const float *orig, const float *filt,
                             const int64_t *roi, double rms_o, double rms_f, double nsig,
                             double beam, afd_fdiag *out);
 
+/* Bounds checks (a debug build of the library compiled with -DAFD_CHECK):
+ * the kernels check their hand-computed shared-memory and global indices,
+ * skip an access that would fall outside its buffer and record the number
+ * of such violations, the first one's code and its index.  This call
+ * synchronises the context's stream, returns the record (HOST ints) and
+ * clears it.  In the release build nothing is recorded: *count is 0.
+ * afd_checked_build() is 1 in the checked build, else 0. */
+afd_status afd_check_violations(afd_ctx *ctx, int *count, int *code, int *index);
+int afd_checked_build(void);
+
 /* Pass timing, for profiling: while on, every float32 filter call that runs
  * on the streaming kernel records a pair of CUDA events on the context's
  * stream around its sequence of passes (after the statistics of

@@ -15,6 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libafd.so")
+# the debug build with bounds checks in the kernels (-DAFD_CHECK)
+LIB_CHECKED = os.path.join(HERE, "libafd_check.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["afd_api.cu", "pm_simple.cu", "pm_stream.cu", "reduce.cu", "selftest.cu",
@@ -22,7 +24,7 @@ SOURCES = ["afd_api.cu", "pm_simple.cu", "pm_stream.cu", "reduce.cu", "selftest.
            "pm_tb_bf16.cu", "pm_tb_i16.cu", "pm_batch.cu",
            "serve.cu", "fdiag.cu", "smooth.cu"]
 HEADERS = ["afd_math.cuh", "afd_ptx.cuh", "afd_internal.h", "afd_store.cuh", "pm_tb.cuh",
-           "pm_tb_impl.cuh", "afd_ctx.h", "afd_batch.h"]
+           "pm_tb_impl.cuh", "afd_ctx.h", "afd_batch.h", "afd_trace.h", "afd_check.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no multiply/add contraction of scalar code anywhere; every FMA
 # the kernels want is written explicitly (afd_math.cuh also guards the packed
@@ -45,8 +47,8 @@ def _newest_input() -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
-def up_to_date() -> bool:
-    return os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input()
+def up_to_date(lib: str = LIB) -> bool:
+    return os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input()
 
 
 def _extra_flags():
@@ -55,9 +57,10 @@ def _extra_flags():
     return os.environ.get("AFD_NVCC_FLAGS", "").split()
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, *_extra_flags(), "-c", os.path.join(CSRC, src), "-o", obj]
+def _compile(src: str, verbose: bool, objdir: str = BUILD, defines=()) -> str:
+    obj = os.path.join(objdir, os.path.splitext(src)[0] + ".o")
+    cmd = [nvcc(), *ARCH, *FLAGS, *defines, *_extra_flags(), "-c", os.path.join(CSRC, src),
+           "-o", obj]
     if verbose:
         cmd[1:1] = ["-Xptxas", "-v"]
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -68,23 +71,28 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every kernel and the C ABI into libafd.so (in-tree)."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every kernel and the C ABI into libafd.so (in-tree); with
+    checked=True, the bounds-checked debug build libafd_check.so instead."""
+    lib = LIB_CHECKED if checked else LIB
+    objdir = os.path.join(BUILD, "checked") if checked else BUILD
+    defines = ("-DAFD_CHECK",) if checked else ()
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(objdir, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+        objs = list(ex.map(lambda s: _compile(s, verbose, objdir, defines), SOURCES))
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-ldl", "-lrt",
            "-lpthread"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (res.stdout, res.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

@@ -16,6 +16,9 @@ import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libafd.so")
+# AFD_LIB selects another build of the same ABI (the bounds-checked debug
+# build, libafd_check.so); there is no fallback if it is missing either.
+LIB_PATH = os.environ.get("AFD_LIB", LIB_PATH)
 
 AFD_OK, AFD_EINVAL, AFD_ENOMEM, AFD_ECUDA, AFD_ETIMEOUT, AFD_EBUSY = range(6)
 COND = {"exponential": 0, "rational": 1}
@@ -55,6 +58,9 @@ def _load():
         "afd_smooth_box": ([vp, vp, vp, i64, i64, i64, vp], c_int),
         "afd_smooth_gauss": ([vp, vp, vp, i64, i64, i64, vp, vp, f32], c_int),
         "afd_pass_timing": ([vp, c_int], c_int),
+        "afd_check_violations": ([vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                  ctypes.POINTER(c_int)], c_int),
+        "afd_checked_build": ([], c_int),
         "afd_pass_timing_read": ([vp, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int64)], c_int),
         "afd_filter_intensity": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, f32, c_int], c_int),
@@ -332,6 +338,19 @@ def afd_f_diagnostic(ctx: Context, orig: torch.Tensor, filt: torch.Tensor,
                                  float(rms_f), float(nsig), float(beam), ctypes.byref(r)),
            "afd_f_diagnostic", ctx)
     return {name: getattr(r, name) for name, _ in FDiag._fields_}
+
+
+def afd_check_violations(ctx: Context):
+    """(count, first code, first index) of the bounds-check violations since
+    the last call (always count 0 in the release build); clears them."""
+    n, code, idx = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib.afd_check_violations(ctx.handle, ctypes.byref(n), ctypes.byref(code),
+                                     ctypes.byref(idx)), "afd_check_violations", ctx)
+    return n.value, code.value, idx.value
+
+
+def afd_checked_build() -> bool:
+    return bool(_lib.afd_checked_build())
 
 
 def afd_pass_timing(ctx: Context, on: bool) -> None:

@@ -19,6 +19,8 @@
 
 #include "../../include/afd.h"
 #include "afd_ctx.h"
+#include "afd_trace.h"
+#include "afd_check.cuh"
 #include "afd_internal.h"
 #include "afd_store.cuh"
 
@@ -284,6 +286,7 @@ afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int
         for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
             const float *src = src_of(i);
             const int m = (src == in) ? 0 : (src == out ? 1 : 2);
+            const afd_host::TraceRange pass_trace("pass");
             afd::StreamPlan pl = plan;
             pl.pdl = i > 0;
             pl.kdev = kdev;
@@ -550,6 +553,7 @@ afd_status afd_set_stream_zchunk(afd_ctx *ctx, int zc)
 afd_status afd_filter(afd_ctx *ctx, float *cube, int64_t nx, int64_t ny, int64_t nz,
                       const float *spacing, float K, float dt, int n_iter, afd_conductance cond)
 {
+    const afd_host::TraceRange trace_("afd_filter");
     if (!ctx || !cube || !dims_ok(nx, ny, nz) || !params_ok(spacing, K, dt, n_iter, cond))
         return AFD_EINVAL;
     afd_status st = set_device(ctx);
@@ -562,6 +566,7 @@ afd_status afd_filter_out(afd_ctx *ctx, const float *in, float *out, int64_t nx,
                           int64_t nz, const float *spacing, float K, float dt, int n_iter,
                           afd_conductance cond)
 {
+    const afd_host::TraceRange trace_("afd_filter_out");
     if (!ctx || !in || !out || !dims_ok(nx, ny, nz) ||
         !params_ok(spacing, K, dt, n_iter, cond))
         return AFD_EINVAL;
@@ -582,6 +587,7 @@ afd_status afd_filter_rel(afd_ctx *ctx, const float *in, float *out, int64_t nx,
                           int64_t nz, const float *spacing, float k_rms, float dt, int n_iter,
                           afd_conductance cond, float *K_out)
 {
+    const afd_host::TraceRange trace_("afd_filter_rel");
     if (!ctx || !in || !out || !dims_ok(nx, ny, nz) || !(k_rms > 0.0f) || !std::isfinite(k_rms) ||
         !params_ok(spacing, 1.0f, dt, n_iter, cond))
         return AFD_EINVAL;
@@ -646,6 +652,7 @@ afd_status afd_f_diagnostic(afd_ctx *ctx, const float *orig, const float *filt,
                             const int64_t *roi, double rms_o, double rms_f, double nsig,
                             double beam, afd_fdiag *out)
 {
+    const afd_host::TraceRange trace_("afd_f_diagnostic");
     if (!ctx || !orig || !filt || !out || !dims_ok(nx, ny, nz) || !(nsig > 0.0) ||
         !std::isfinite(nsig) || !(beam >= 1.0) || !std::isfinite(beam) || std::isnan(rms_o) ||
         std::isnan(rms_f) || std::isinf(rms_o) || std::isinf(rms_f))
@@ -764,7 +771,7 @@ afd_status smooth_separable(afd_ctx *ctx, const float *in, float *out, int nx, i
             return st;
         e = afd::launch_smooth_sep_tma(map, out, nx, ny, nz, w, hx, ctx->d_err, ctx->stream);
     } else {
-        e = afd::launch_smooth_sep(in, out, nx, ny, nz, w, ctx->stream);
+        e = afd::launch_smooth_sep(in, out, nx, ny, nz, w, ctx->d_err, ctx->stream);
     }
     ctx->launches++;
     return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
@@ -774,6 +781,7 @@ afd_status smooth_separable(afd_ctx *ctx, const float *in, float *out, int nx, i
 afd_status afd_smooth_box(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
                           int64_t nz, const int *N)
 {
+    const afd_host::TraceRange trace_("afd_smooth_box");
     if (!ctx || !in || !out || !N || !dims_ok(nx, ny, nz) || !cubes_disjoint(in, out, nx * ny * nz))
         return AFD_EINVAL;
     for (int a = 0; a < 3; ++a)
@@ -800,6 +808,7 @@ afd_status afd_smooth_gauss(afd_ctx *ctx, const float *in, float *out, int64_t n
                             int64_t nz, const float *fwhm, const float *angles_deg,
                             float truncate)
 {
+    const afd_host::TraceRange trace_("afd_smooth_gauss");
     if (!ctx || !in || !out || !fwhm || !dims_ok(nx, ny, nz) ||
         !cubes_disjoint(in, out, nx * ny * nz))
         return AFD_EINVAL;
@@ -888,7 +897,7 @@ afd_status afd_smooth_gauss(afd_ctx *ctx, const float *in, float *out, int64_t n
             e = cudaStreamSynchronize(ctx->stream);  // W is a local buffer
         if (e == cudaSuccess)
             e = afd::launch_smooth_direct(in, out, inx, iny, inz, ctx->fd_buf, r[0], r[1], r[2],
-                                          static_cast<float>(wsum), ctx->stream);
+                                          static_cast<float>(wsum), ctx->d_err, ctx->stream);
     }
     ctx->launches++;
     return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
@@ -898,6 +907,7 @@ afd_status afd_filter_intensity(afd_ctx *ctx, const float *in, float *out, int64
                                 int64_t ny, int64_t nz, const float *C, float K, float rms,
                                 float tau, int n_iter)
 {
+    const afd_host::TraceRange trace_("afd_filter_intensity");
     if (!ctx || !in || !out || !C || !dims_ok(nx, ny, nz) || n_iter < 0)
         return AFD_EINVAL;
     for (int a = 0; a < 3; ++a)
@@ -1013,6 +1023,7 @@ afd_status afd_filter_host(afd_ctx *ctx, const float *host_in, float *host_out, 
                            int64_t ny, int64_t nz, const float *spacing, float K, float dt,
                            int n_iter, afd_conductance cond)
 {
+    const afd_host::TraceRange trace_("afd_filter_host");
     if (!host_args_ok(ctx, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter, cond))
         return AFD_EINVAL;
     afd_status st = set_device(ctx);
@@ -1028,6 +1039,7 @@ afd_status afd_filter_host_async(afd_ctx *ctx, const float *host_in, float *host
                                  int64_t ny, int64_t nz, const float *spacing, float K, float dt,
                                  int n_iter, afd_conductance cond)
 {
+    const afd_host::TraceRange trace_("afd_filter_host_async");
     if (!host_args_ok(ctx, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter, cond))
         return AFD_EINVAL;
     afd_status st = set_device(ctx);
@@ -1044,6 +1056,7 @@ afd_status afd_filter_host_async(afd_ctx *ctx, const float *host_in, float *host
 afd_status afd_quantize(afd_ctx *ctx, const float *in, void *out, int64_t n, afd_storage storage,
                         float scale)
 {
+    const afd_host::TraceRange trace_("afd_quantize");
     if (!ctx || !in || !out || n < 1 || !storage_ok(storage) || storage == AFD_F32 ||
         !pow2_scale_ok(scale))
         return AFD_EINVAL;
@@ -1059,6 +1072,7 @@ afd_status afd_quantize(afd_ctx *ctx, const float *in, void *out, int64_t n, afd
 afd_status afd_dequantize(afd_ctx *ctx, const void *in, float *out, int64_t n,
                           afd_storage storage, float scale)
 {
+    const afd_host::TraceRange trace_("afd_dequantize");
     if (!ctx || !in || !out || n < 1 || !storage_ok(storage) || storage == AFD_F32 ||
         !pow2_scale_ok(scale))
         return AFD_EINVAL;
@@ -1075,6 +1089,7 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
                          float scale, int64_t nx, int64_t ny, int64_t nz, const float *spacing,
                          float K, float dt, int n_iter, afd_conductance cond, int t_block)
 {
+    const afd_host::TraceRange trace_("afd_filter_ex");
     if (!ctx || !in || !out || !storage_ok(storage) || !dims_ok(nx, ny, nz) ||
         !params_ok(spacing, K, dt, n_iter, cond))
         return AFD_EINVAL;
@@ -1160,6 +1175,7 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
     bool tiles_zeroed = false;
     bool prev_stream = false;  // the previous pass was a streaming-kernel launch
     for (int i = 0; i < npass; ++i) {
+        const afd_host::TraceRange pass_trace("pass");
         const int T = depth_of(i);
         if (fits && T == 1) {
             // depth 1: the barrier-free streaming kernel, on the stored format
@@ -1237,6 +1253,7 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
 
 afd_status afd_stats(afd_ctx *ctx, const float *cube, int64_t n, double *out4)
 {
+    const afd_host::TraceRange trace_("afd_stats");
     if (!ctx || !cube || !out4 || n < 1)
         return AFD_EINVAL;
     afd_status st = set_device(ctx);
@@ -1247,6 +1264,7 @@ afd_status afd_stats(afd_ctx *ctx, const float *cube, int64_t n, double *out4)
 
 afd_status afd_noise_rms(afd_ctx *ctx, const float *cube, int64_t n, double *out)
 {
+    const afd_host::TraceRange trace_("afd_noise_rms");
     if (!ctx || !cube || !out || n < 1)
         return AFD_EINVAL;
     afd_status st = set_device(ctx);
@@ -1261,6 +1279,7 @@ afd_status afd_noise_rms(afd_ctx *ctx, const float *cube, int64_t n, double *out
 
 afd_status afd_sum(afd_ctx *ctx, const float *cube, int64_t n, double *out)
 {
+    const afd_host::TraceRange trace_("afd_sum");
     if (!ctx || !cube || !out || n < 1)
         return AFD_EINVAL;
     afd_status st = set_device(ctx);
@@ -1300,6 +1319,29 @@ afd_status afd_sync(afd_ctx *ctx)
     }
     return AFD_OK;
 }
+
+afd_status afd_check_violations(afd_ctx *ctx, int *count, int *code, int *index)
+{
+    if (!ctx || !count || !code || !index)
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    int rec[3] = {0, 0, 0};
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(rec, ctx->d_err + afd::kCheckCount, sizeof(rec), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemset(ctx->d_err + afd::kCheckCount, 0, sizeof(rec));
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    *count = rec[0];
+    *code = rec[1];
+    *index = rec[2];
+    return AFD_OK;
+}
+
+int afd_checked_build(void) { return afd::kChecked ? 1 : 0; }
 
 afd_status afd_pass_timing(afd_ctx *ctx, int on)
 {

@@ -155,11 +155,11 @@ struct SepWeights {
     int rx, ry, rz;
 };
 cudaError_t launch_smooth_sep(const float *in, float *out, int nx, int ny, int nz,
-                              const SepWeights &w, cudaStream_t stream);
+                              const SepWeights &w, int *err, cudaStream_t stream);
 // Direct correlation with W (device, x fastest) of (2rx+1)(2ry+1)(2rz+1).
 // wsum: the total weight (the divisor of voxels whose window is inside).
 cudaError_t launch_smooth_direct(const float *in, float *out, int nx, int ny, int nz,
-                                 const float *W, int rx, int ry, int rz, float wsum,
+                                 const float *W, int rx, int ry, int rz, float wsum, int *err,
                                  cudaStream_t stream);
 size_t smooth_direct_smem(int rx, int ry, int rz);  // bytes of shared memory it needs
 // The separable pass with TMA-streamed planes: nx % 4 == 0, 16-byte aligned

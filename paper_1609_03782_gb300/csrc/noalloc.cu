@@ -29,6 +29,7 @@
 
 #include "../../include/afd.h"
 #include "afd_internal.h"
+#include "afd_trace.h"
 
 namespace {
 
@@ -114,6 +115,7 @@ extern "C" afd_status afd_filter_noalloc(const float *in, float *out, int64_t nx
                                          int64_t nz, const float *spacing, float K, float dt,
                                          int n_iter, afd_conductance cond, void *cuda_stream)
 {
+    const afd_host::TraceRange trace_("afd_filter_noalloc");
     // ---- arguments (the same rules as afd_filter_out) ----
     if (!in || !out || nx < 1 || ny < 1 || nz < 1)
         return AFD_EINVAL;

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "afd_batch.h"
+#include "afd_trace.h"
 #include "afd_ctx.h"
 #include "afd_internal.h"
 #include "afd_store.cuh"
@@ -455,6 +456,7 @@ afd_status afd_batch_get(afd_batch *b, int i, void *cube)
 afd_status afd_batch_filter(afd_batch *b, const float *K, const float *spacing, float dt,
                             int n_iter, afd_conductance cond)
 {
+    const afd_host::TraceRange trace_("afd_batch_filter");
     if (!b || !K || !params_ok(spacing, 1.0f, dt, n_iter, cond) || n_iter < 1)
         return AFD_EINVAL;
     bool lin = false, fin = false;

@@ -33,6 +33,7 @@
 // (afd_ptx.cuh).
 #include "afd_internal.h"
 #include "afd_ptx.cuh"
+#include "afd_check.cuh"
 #include "afd_store.cuh"
 
 namespace afd {
@@ -303,6 +304,8 @@ struct PlaneArgs {
     bool edge, act0, act1;
     typename Store<S>::T *out0;
     int64_t row_stride;
+    const typename Store<S>::T *obase;  // the output cube and its extent in
+    int64_t oext;                        // elements (bounds checks only)
 };
 
 // One plane z of the block: reads the plane above (waiting for its TMA),
@@ -380,9 +383,9 @@ __device__ __forceinline__ bool plane_step(const PlaneArgs<S> &a, const Packed &
     const Q o1 = {update2<C>(cur1.a, sx1.a, f2_sub(fup.a, fmid.a), f2_sub(fa1.a, fb1.a), k.ai, k.one),
                   update2<C>(cur1.b, sx1.b, f2_sub(fup.b, fmid.b), f2_sub(fa1.b, fb1.b), k.ai, k.one)};
     typename Store<S>::T *po = a.out0 + static_cast<int64_t>(z) * a.ny * a.row_stride;
-    if (a.act0)
+    if (a.act0 && check_range(a.err, po - a.obase, 0, a.oext - 3, kChkStreamStore))
         stg_q<S>(po, o0);
-    if (a.act1)
+    if (a.act1 && check_range(a.err, po + a.row_stride - a.obase, 0, a.oext - 3, kChkStreamStore))
         stg_q<S>(po + a.row_stride, o1);
 
     __syncwarp();
@@ -458,9 +461,19 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
     // ---------------- consumers ----------------
     const int qx = threadIdx.x & 15;
     const int ry = threadIdx.x >> 4;
-    const int r0 = 1 + 2 * ry;                       // slot row of the first row
-    const int cen0 = r0 * SL::PX + SL::HX + 4 * qx;  // quad of row 0 in a slot (elements)
-    const int cen1 = cen0 + SL::PX;                  // quad of row 1
+    const int r0 = 1 + 2 * ry;                 // slot row of the first row
+    int cen0 = r0 * SL::PX + SL::HX + 4 * qx;  // quad of row 0 in a slot (elements)
+    int cen1 = cen0 + SL::PX;                  // quad of row 1
+    // the block reads slot elements [cen0 - PX, cen1 + PX + 4); a thread
+    // that would leave the slot (checked builds) reads a safe block instead
+    // and stores nothing
+    const bool slot_ok =
+        check_range(err, cen0 - SL::PX, 0, SL::PX * PY, kChkStreamSlot) &&
+        check_range(err, cen1 + SL::PX + 3, 0, SL::PX * PY, kChkStreamSlot);
+    if (!slot_ok) {
+        cen0 = SL::PX + SL::HX;
+        cen1 = cen0 + SL::PX;
+    }
     uint32_t kk = 0;
 
     for (;;) {
@@ -486,8 +499,13 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
         const int x = tc.x0 + 4 * qx;
         const int ya = tc.y0 + 2 * ry;  // row 0
         const int yb = ya + 1;          // row 1
-        const bool act0 = (x < nx) && (ya < ny);
-        const bool act1 = (x < nx) && (yb < ny);
+        const bool tile_ok =
+            check_range(err, tc.z1, tc.z0 + 1, static_cast<int64_t>(nz) + 1, kChkStreamTile) &&
+            check_range(err, tc.x0, 0, nx, kChkStreamTile) &&
+            check_range(err, tc.y0, 0, ny, kChkStreamTile) &&
+            check_range(err, tc.zlo, 0, nz, kChkStreamTile);
+        const bool act0 = slot_ok && tile_ok && (x < nx) && (ya < ny);
+        const bool act1 = slot_ok && tile_ok && (x < nx) && (yb < ny);
         const bool edge = (tc.x0 == 0) || (tc.x0 + TX >= nx) || (tc.y0 == 0) ||
                           (tc.y0 + TY >= ny);
         const uint32_t kbase = kk;
@@ -530,7 +548,8 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
         }
 
         const PlaneArgs<S> pa{slots, full, empty, err, kbase, tc.zlo, nx, ny, nz, cen0, cen1,
-                              x, ya, yb, lane, edge, act0, act1, out0, row_stride};
+                              x, ya, yb, lane, edge, act0, act1, out0, row_stride, tc.out,
+                              static_cast<int64_t>(nz) * ny * row_stride};
         // two planes per iteration with the register roles swapped: no copies
         Q n0, n1, fa0, fa1;
         int z = tc.z0;

@@ -36,6 +36,7 @@
 #include "afd_internal.h"
 #include "afd_ptx.cuh"
 #include "afd_store.cuh"
+#include "afd_check.cuh"
 
 namespace afd {
 namespace tb {
@@ -227,12 +228,25 @@ __global__ void __launch_bounds__(Geom<T>::THREADS, Geom<T>::MIN_BLOCKS)
     const int rp = item / G::QX;
     const int col = 4 + 4 * qx;              // block column in a stage plane
     const int rowa = 1 + 2 * rp;             // block's first row in a stage plane
-    const int ra = rowa * G::BW + col;       // offsets of the block's rows
-    const int rb = ra + G::BW;
+    int ra = rowa * G::BW + col;       // offsets of the block's rows
+    int rb = ra + G::BW;
     const int rcol = (R::HX - G::HC + 4 * qx) * R::ES;  // byte column in a ring slot
     const int rrow = 2 * rp;                           // first row in a ring slot
-    const int ring_a = rrow * R::W * R::ES + rcol;
-    const int ring_b = ring_a + R::W * R::ES;
+    int ring_a = rrow * R::W * R::ES + rcol;
+    int ring_b = ring_a + R::W * R::ES;
+    // the block reads stage-plane floats [ra - BW, rb + BW + 4) and ring-slot
+    // bytes [ring_a, ring_b + 4 ES); a thread that would leave them (checked
+    // builds) works on a safe block and stores nothing
+    const bool blk_ok = check_range(err, ra - G::BW, 0, G::BFLOATS, kChkTbSmem) &&
+                        check_range(err, rb + G::BW + 3, 0, G::BFLOATS, kChkTbSmem) &&
+                        check_range(err, ring_a, 0, R::SLOT_BYTES, kChkTbSmem) &&
+                        check_range(err, ring_b + 4 * R::ES - 1, 0, R::SLOT_BYTES, kChkTbSmem);
+    if (!blk_ok) {
+        ra = G::BW + 4;
+        rb = ra + G::BW;
+        ring_a = 0;
+        ring_b = R::W * R::ES;
+    }
 
     uint32_t kk = 0, g = 0;
     const int64_t txy = static_cast<int64_t>(tiles_x) * tiles_y;
@@ -357,9 +371,12 @@ __global__ void __launch_bounds__(Geom<T>::THREADS, Geom<T>::MIN_BLOCKS)
                     } else if (p >= z0 && p < z1) {
                         E *po = out + (static_cast<int64_t>(p) * ny + ya) * static_cast<int64_t>(nx) +
                                 xb;
-                        if (out_a)
+                        const int64_t oext = static_cast<int64_t>(nz) * ny * nx - 3;
+                        if (out_a && blk_ok &&
+                            check_range(err, po - out, 0, oext, kChkTbStore))
                             store_block<S>(po, o0);
-                        if (out_b)
+                        if (out_b && blk_ok &&
+                            check_range(err, po + nx - out, 0, oext, kChkTbStore))
                             store_block<S>(po + nx, o1);
                     }
                 }

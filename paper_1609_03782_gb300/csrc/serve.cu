@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "afd_batch.h"
+#include "afd_trace.h"
 #include "afd_store.cuh"
 
 namespace {
@@ -395,6 +396,7 @@ afd_status afd_serve_submit(afd_serve *s, int cube, float K, float dt, int n_ite
 
 afd_status afd_serve_step(afd_serve *s, int wait, int *active, int *queued)
 {
+    const afd_host::TraceRange trace_("afd_serve_step");
     if (!s)
         return AFD_EINVAL;
     afd_status st = set_device(s->ctx);

@@ -22,6 +22,7 @@
 
 #include "afd_internal.h"
 #include "afd_ptx.cuh"
+#include "afd_check.cuh"
 
 namespace afd {
 namespace {
@@ -33,7 +34,7 @@ constexpr int kSmThreads = 256;
 template <int RZ>
 __global__ void __launch_bounds__(kSmThreads)
     smooth_sep(const float *__restrict__ in, float *__restrict__ out, int nx, int ny, int nz,
-               int tiles_x, int tiles_y, int zc, const __grid_constant__ SepWeights w)
+               int tiles_x, int tiles_y, int zc, const __grid_constant__ SepWeights w, int *err)
 {
     extern __shared__ float sm[];
     const int rx = w.rx, ry = w.ry;
@@ -101,6 +102,8 @@ __global__ void __launch_bounds__(kSmThreads)
         // ---- 2: x convolution of every row, 4 outputs per task
         for (int task = tid; task < PH * 16; task += kSmThreads) {
             const int r = task >> 4, q = task & 15;
+            if (!check_range(err, r * PW + 4 * q + 2 * rx + 4, 0, PH * PW, kChkSmoothSmem))
+                continue;
             const float *row = P + r * PW + 4 * q;
             float v0 = row[0], v1 = row[1], v2 = row[2], v3 = row[3];
             float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
@@ -121,7 +124,9 @@ __global__ void __launch_bounds__(kSmThreads)
         __syncthreads();
         // ---- 3: y convolution, into the z ring
         float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int k = 0; k <= 2 * ry; ++k) {
+        const bool y_ok = check_range(err, (ty + 2 * ry) * SX + 4 * qx + 3, 0, PH * SX,
+                                      kChkSmoothSmem);
+        for (int k = 0; k <= 2 * ry && y_ok; ++k) {
             const float wk = w.wy[k];
             const float4 v = *reinterpret_cast<const float4 *>(X + (ty + k) * SX + 4 * qx);
             c[0] = __fmaf_rn(wk, v.x, c[0]);
@@ -160,7 +165,9 @@ __global__ void __launch_bounds__(kSmThreads)
             float *dst = out + (static_cast<int64_t>(zo) * ny + yr) * nx;
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                if (xq + j < nx)
+                if (xq + j < nx &&
+                    check_range(err, dst + xq + j - out, 0, static_cast<int64_t>(nz) * ny * nx,
+                                kChkSmoothStore))
                     dst[xq + j] = o[j];
         }
         // the next iteration rewrites P right away: every read of P happened
@@ -280,6 +287,9 @@ __global__ void __launch_bounds__(kSmTmaThreads)
             // read is column hx + 4q + rx + 3 <= SW - 1 (hx >= rx)
             for (int task = tid; task < SH * 16; task += kSmThreads) {
                 const int r = task >> 4, q = task & 15;
+                if (!(check_range(err, r * SW + hx + 4 * q - rx, 0, SH * SW, kChkSmoothSmem) &&
+                      check_range(err, r * SW + hx + 4 * q + rx + 3, 0, SH * SW, kChkSmoothSmem)))
+                    continue;
                 const float *row = S + r * SW + hx + 4 * q - rx;
                 float v0 = row[0], v1 = row[1], v2 = row[2];
                 float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
@@ -304,7 +314,7 @@ __global__ void __launch_bounds__(kSmTmaThreads)
         // before this barrier
         consumer_barrier();
         float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (have) {
+        if (have && check_range(err, (ty + 2 * ry) * SX + 4 * qx + 3, 0, SH * SX, kChkSmoothSmem)) {
             for (int k = 0; k <= 2 * ry; ++k) {
                 const float wk = w.wy[k];
                 const float4 v = *reinterpret_cast<const float4 *>(Xb + (ty + k) * SX + 4 * qx);
@@ -342,8 +352,9 @@ __global__ void __launch_bounds__(kSmTmaThreads)
                 o[jj] = __fmul_rn(__fmul_rn(sum, inv_xy[jj]), inv_z);
             }
             // nx % 4 == 0 and xq % 4 == 0: the quad is inside the row
-            *reinterpret_cast<float4 *>(out + (static_cast<int64_t>(zo) * ny + yr) * nx + xq) =
-                make_float4(o[0], o[1], o[2], o[3]);
+            const int64_t oi = (static_cast<int64_t>(zo) * ny + yr) * nx + xq;
+            if (check_range(err, oi, 0, static_cast<int64_t>(nz) * ny * nx - 3, kChkSmoothStore))
+                *reinterpret_cast<float4 *>(out + oi) = make_float4(o[0], o[1], o[2], o[3]);
         }
     }
 }
@@ -357,7 +368,7 @@ __global__ void __launch_bounds__(kSmTmaThreads)
 __global__ void __launch_bounds__(kSmThreads)
     smooth_direct(const float *__restrict__ in, float *__restrict__ out, int nx, int ny, int nz,
                   int tiles_x, int tiles_y, int zc, const float *__restrict__ W, int rx, int ry,
-                  int rz, float wsum)
+                  int rz, float wsum, int *err)
 {
     extern __shared__ float sm[];
     const int WX = 2 * rx + 1, WY = 2 * ry + 1, WZ = 2 * rz + 1;
@@ -402,7 +413,10 @@ __global__ void __launch_bounds__(kSmThreads)
         }
         __syncthreads();
         const int zo = zi - rz;  // every plane of its window is now in the ring
-        if (zo >= zs && yr < ny) {
+        // the farthest ring read of this thread: row ty + 2 ry, column 4 qx + 2 rx + 3
+        if (zo >= zs && yr < ny &&
+            check_range(err, (ty + 2 * ry) * PW + 4 * qx + 2 * rx + 3, 0, PH * PW,
+                        kChkSmoothSmem)) {
             float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
             for (int dz = 0; dz < WZ; ++dz) {
                 const int qz = zo - rz + dz;
@@ -454,7 +468,9 @@ __global__ void __launch_bounds__(kSmThreads)
             float *dst = out + (static_cast<int64_t>(zo) * ny + yr) * nx;
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                if (xq + j < nx)
+                if (xq + j < nx &&
+                    check_range(err, dst + xq + j - out, 0, static_cast<int64_t>(nz) * ny * nx,
+                                kChkSmoothStore))
                     dst[xq + j] = __fdiv_rn(a[j], d[j]);
         }
         __syncthreads();  // the ring slot of plane zi - 2 rz is refilled next
@@ -463,7 +479,7 @@ __global__ void __launch_bounds__(kSmThreads)
 
 template <int RZ>
 cudaError_t sep_launch(const float *in, float *out, int nx, int ny, int nz, const SepWeights &w,
-                       int zc, cudaStream_t stream)
+                       int zc, int *err, cudaStream_t stream)
 {
     const int tiles_x = (nx + SX - 1) / SX, tiles_y = (ny + SY - 1) / SY;
     const int tiles_z = (nz + zc - 1) / zc;
@@ -474,7 +490,7 @@ cudaError_t sep_launch(const float *in, float *out, int nx, int ny, int nz, cons
     if (e != cudaSuccess)
         return e;
     smooth_sep<RZ><<<tiles_x * tiles_y * tiles_z, kSmThreads, smem, stream>>>(
-        in, out, nx, ny, nz, tiles_x, tiles_y, zc, w);
+        in, out, nx, ny, nz, tiles_x, tiles_y, zc, w, err);
     return cudaGetLastError();
 }
 
@@ -522,7 +538,7 @@ struct SepTable;
 template <>
 struct SepTable<> {
     static cudaError_t run(int, const float *, float *, int, int, int, const SepWeights &, int,
-                           cudaStream_t)
+                           int *, cudaStream_t)
     {
         return cudaErrorInvalidValue;
     }
@@ -530,11 +546,11 @@ struct SepTable<> {
 template <int R0, int... R>
 struct SepTable<R0, R...> {
     static cudaError_t run(int rz, const float *in, float *out, int nx, int ny, int nz,
-                           const SepWeights &w, int zc, cudaStream_t s)
+                           const SepWeights &w, int zc, int *err, cudaStream_t s)
     {
         if (rz == R0)
-            return sep_launch<R0>(in, out, nx, ny, nz, w, zc, s);
-        return SepTable<R...>::run(rz, in, out, nx, ny, nz, w, zc, s);
+            return sep_launch<R0>(in, out, nx, ny, nz, w, zc, err, s);
+        return SepTable<R...>::run(rz, in, out, nx, ny, nz, w, zc, err, s);
     }
 };
 
@@ -572,18 +588,18 @@ size_t smooth_direct_smem(int rx, int ry, int rz)
 }
 
 cudaError_t launch_smooth_sep(const float *in, float *out, int nx, int ny, int nz,
-                              const SepWeights &w, cudaStream_t stream)
+                              const SepWeights &w, int *err, cudaStream_t stream)
 {
     if (w.rx < 0 || w.rx > kSepMaxR || w.ry < 0 || w.ry > kSepMaxR || w.rz < 0 ||
         w.rz > kSepMaxRz)
         return cudaErrorInvalidValue;
     const int zc = nz < 64 ? nz : 64;
     return SepTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12>::run(w.rz, in, out, nx, ny, nz, w,
-                                                                  zc, stream);
+                                                                  zc, err, stream);
 }
 
 cudaError_t launch_smooth_direct(const float *in, float *out, int nx, int ny, int nz,
-                                 const float *W, int rx, int ry, int rz, float wsum,
+                                 const float *W, int rx, int ry, int rz, float wsum, int *err,
                                  cudaStream_t stream)
 {
     const size_t smem = smooth_direct_smem(rx, ry, rz);
@@ -595,7 +611,7 @@ cudaError_t launch_smooth_direct(const float *in, float *out, int nx, int ny, in
     const int zc = nz < 32 ? nz : 32;
     const int tiles_z = (nz + zc - 1) / zc;
     smooth_direct<<<tiles_x * tiles_y * tiles_z, kSmThreads, smem, stream>>>(
-        in, out, nx, ny, nz, tiles_x, tiles_y, zc, W, rx, ry, rz, wsum);
+        in, out, nx, ny, nz, tiles_x, tiles_y, zc, W, rx, ry, rz, wsum, err);
     return cudaGetLastError();
 }
 
