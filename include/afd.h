@@ -229,7 +229,9 @@ afd_status afd_dequantize(afd_ctx *ctx, const void *in, float *out, int64_t n,
  *   scale     the cube's power-of-two scale (ignored for AFD_F32).
  *   K         in the cube's value units (value = stored value * scale).
  *   spacing, dt, n_iter, cond   as for afd_filter.
- *   t_block   1, 2, 4 or 8 (0 = 4 for 2-byte storage, 2 for float32).
+ *   t_block   1, 2, 4 or 8 (0 = 1: one iteration per pass on the
+ *             streaming kernel, which on GB300 outruns every blocked depth;
+ *             tune.Tuner.tune_filter_ex picks a depth by timing).
  * Each pass reads the stored cube, runs its iterations in float32 with the
  * arithmetic of afd_filter, and rounds the result once into the storage
  * format; n_iter = (n_iter / T) passes of depth T, the remainder as passes

@@ -1098,7 +1098,7 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
     if (!pow2_scale_ok(scale))
         return AFD_EINVAL;
     if (t_block == 0)
-        t_block = (storage == AFD_F32) ? 2 : 4;
+        t_block = 1;  // the streaming pass: faster on GB300 than any blocked depth
     if (!afd::tb_depth_ok(t_block))
         return AFD_EINVAL;
     const int S = storage;
