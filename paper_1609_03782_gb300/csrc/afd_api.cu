@@ -885,19 +885,40 @@ afd_status afd_smooth_gauss(afd_ctx *ctx, const float *in, float *out, int64_t n
                     W[(dx + r[0]) + WX * ((dy + r[1]) + WY * (dz + r[2]))] = wq;
                     wsum += static_cast<double>(wq);
                 }
+        // FP64 prefix sums of W for the in-cube weight near a face
+        const int SX1 = WX + 1, SY1 = WY + 1;
+        std::vector<double> S(static_cast<size_t>(SX1) * SY1 * (WZ + 1), 0.0);
+        for (int k = 1; k <= WZ; ++k)
+            for (int j = 1; j < SY1; ++j)
+                for (int i = 1; i < SX1; ++i) {
+                    const size_t o = (static_cast<size_t>(k) * SY1 + j) * SX1 + i;
+                    const size_t pz = static_cast<size_t>(SX1) * SY1;
+                    S[o] = static_cast<double>(W[(i - 1) + WX * ((j - 1) + WY * (k - 1))]) +
+                           S[o - 1] + S[o - SX1] + S[o - pz] - S[o - SX1 - 1] - S[o - pz - 1] -
+                           S[o - pz - SX1] + S[o - pz - SX1 - 1];
+                }
+        const size_t w_bytes = (W.size() * sizeof(float) + 15) & ~size_t(15);
+        const size_t s_bytes = S.size() * sizeof(double);
         st = ensure_buffer(ctx, &ctx->fd_buf, &ctx->fd_bytes,
-                           std::max(ctx->fd_bytes, W.size() * sizeof(float)));
+                           std::max(ctx->fd_bytes, w_bytes + s_bytes));
         if (st != AFD_OK)
             return st;
         // the weights share the diagnostic's scratch: stream-ordered, copied
         // from host memory before the kernel that reads them
-        e = cudaMemcpyAsync(ctx->fd_buf, W.data(), W.size() * sizeof(float),
-                            cudaMemcpyHostToDevice, ctx->stream);
+        char *dbuf = reinterpret_cast<char *>(ctx->fd_buf);
+        e = cudaMemcpyAsync(dbuf, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            ctx->stream);
         if (e == cudaSuccess)
-            e = cudaStreamSynchronize(ctx->stream);  // W is a local buffer
+            e = cudaMemcpyAsync(dbuf + w_bytes, S.data(), s_bytes, cudaMemcpyHostToDevice,
+                                ctx->stream);
         if (e == cudaSuccess)
-            e = afd::launch_smooth_direct(in, out, inx, iny, inz, ctx->fd_buf, r[0], r[1], r[2],
-                                          static_cast<float>(wsum), ctx->d_err, ctx->stream);
+            e = cudaStreamSynchronize(ctx->stream);  // W and S are local buffers
+        if (e == cudaSuccess)
+            e = afd::launch_smooth_direct(in, out, inx, iny, inz,
+                                          reinterpret_cast<const float *>(dbuf),
+                                          reinterpret_cast<const double *>(dbuf + w_bytes), r[0],
+                                          r[1], r[2], static_cast<float>(wsum), ctx->d_err,
+                                          ctx->stream);
     }
     ctx->launches++;
     return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);

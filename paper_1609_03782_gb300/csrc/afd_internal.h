@@ -158,9 +158,12 @@ cudaError_t launch_smooth_sep(const float *in, float *out, int nx, int ny, int n
                               const SepWeights &w, int *err, cudaStream_t stream);
 // Direct correlation with W (device, x fastest) of (2rx+1)(2ry+1)(2rz+1).
 // wsum: the total weight (the divisor of voxels whose window is inside).
+// W: the (2rz+1)(2ry+1)(2rx+1) weights, x fastest; S: their FP64 prefix
+// sums, (2rz+2)(2ry+2)(2rx+2) with S[k][j][i] = sum over dz < k, dy < j,
+// dx < i (the in-cube weight of a voxel near a face, by inclusion-exclusion)
 cudaError_t launch_smooth_direct(const float *in, float *out, int nx, int ny, int nz,
-                                 const float *W, int rx, int ry, int rz, float wsum, int *err,
-                                 cudaStream_t stream);
+                                 const float *W, const double *S, int rx, int ry, int rz,
+                                 float wsum, int *err, cudaStream_t stream);
 size_t smooth_direct_smem(int rx, int ry, int rz);  // bytes of shared memory it needs
 // The separable pass with TMA-streamed planes: nx % 4 == 0, 16-byte aligned
 // cubes.  tmap: 3-D float32 map over the input with the box of

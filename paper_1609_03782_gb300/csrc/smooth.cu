@@ -7,17 +7,17 @@
 // W = wx (x) wy (x) wz, and the in-cube weight factorises into per-axis sums,
 // so out = (wz * (wy * (wx * I))) / (Dx(x) Dy(y) Dz(z)) with zero outside the
 // cube, applied as two products with the rounded reciprocals of Dx Dy (per
-// voxel column) and Dz (per plane).  One fused pass streams z: a CTA owns a 64 x 16 column of the cube
-// over a z-chunk; for every input plane it loads the tile and its x/y halo
-// into shared memory (zero outside), convolves along x (a register sliding
-// window per 4 outputs) into a second buffer, then along y, and pushes the
-// result into a register ring of the last 2 RZ + 1 planes per voxel, from
-// which each output plane takes its z sum.  HBM traffic: one read of the
-// input (the halo rows come from L2) and one write.
+// voxel column) and Dz (per plane).  One fused pass streams z: a CTA owns a
+// 64 x 16 column of the cube over a z-chunk; for every input plane it loads
+// the tile and its x/y halo into shared memory (zero outside), convolves
+// along x (a register sliding window per 4 outputs) into a second buffer,
+// then along y, and pushes the result into a register ring of the last
+// 2 RZ + 1 planes per voxel, from which each output plane takes its z sum.
+// HBM traffic: one read of the input (the halo rows come from L2) and one
+// write.
 //
-// Rotated Gaussians are not separable: a direct 3-D correlation keeps the
-// last 2 rz + 1 input planes (tile + halo) in a shared-memory ring and sums
-// all taps per output voxel, four voxels per thread along x.
+// Rotated Gaussians are not separable: their direct 3-D correlation is in
+// smooth_direct.cu.
 #include <cmath>
 
 #include "afd_internal.h"
@@ -359,124 +359,6 @@ __global__ void __launch_bounds__(kSmTmaThreads)
     }
 }
 
-// Direct correlation with a full (2rx+1) x (2ry+1) x (2rz+1) weight array
-// (rotated Gaussian).  Shared memory: the weights, then a ring of 2 rz + 1
-// raw planes of PH x PW (tile + halo).  A voxel whose window lies inside the
-// cube divides by the kernel's total weight wsum (summed in double on the
-// host, rounded once); one within a radius of a face sums the weights of its
-// in-cube taps.
-__global__ void __launch_bounds__(kSmThreads)
-    smooth_direct(const float *__restrict__ in, float *__restrict__ out, int nx, int ny, int nz,
-                  int tiles_x, int tiles_y, int zc, const float *__restrict__ W, int rx, int ry,
-                  int rz, float wsum, int *err)
-{
-    extern __shared__ float sm[];
-    const int WX = 2 * rx + 1, WY = 2 * ry + 1, WZ = 2 * rz + 1;
-    const int PW = SX + 2 * rx + 4;  // + 4: room for the sliding window's reads
-    const int PH = SY + 2 * ry;
-    float *Ws = sm;
-    float *ring = sm + WX * WY * WZ;
-
-    int t = blockIdx.x;
-    const int bx = t % tiles_x;
-    t /= tiles_x;
-    const int by = t % tiles_y;
-    const int bz = t / tiles_y;
-    const int x0 = bx * SX, y0 = by * SY;
-    const int zs = bz * zc, ze = min(zs + zc, nz);
-
-    const int tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
-    const int qx = tid & 15, ty = tid >> 4;
-    const int xq = x0 + 4 * qx, yr = y0 + ty;
-    const bool xy_inside = xq - rx >= 0 && xq + 3 + rx < nx && yr - ry >= 0 && yr + ry < ny;
-
-    for (int i = tid; i < WX * WY * WZ; i += kSmThreads)
-        Ws[i] = W[i];
-
-    for (int zi = zs - rz; zi < ze + rz; ++zi) {
-        // ---- load plane zi into its ring slot (the slot's previous plane,
-        // zi - 2 rz - 1, was last read before the barrier ending the
-        // previous iteration)
-        float *P = ring + ((zi - (zs - rz)) % WZ) * PH * PW;
-        const bool zin = zi >= 0 && zi < nz;
-        const float *src = in + static_cast<int64_t>(zi) * nx * ny;
-        for (int r = warp; r < PH; r += kSmThreads / 32) {
-            const int gy = y0 - ry + r;
-            const bool yin = zin && gy >= 0 && gy < ny;
-            for (int c = lane; c < PW; c += 32) {
-                const int gx = x0 - rx + c;
-                P[r * PW + c] = (yin && gx >= 0 && gx < nx)
-                                    ? __ldg(src + static_cast<int64_t>(gy) * nx + gx)
-                                    : 0.0f;
-            }
-        }
-        __syncthreads();
-        const int zo = zi - rz;  // every plane of its window is now in the ring
-        // the farthest ring read of this thread: row ty + 2 ry, column 4 qx + 2 rx + 3
-        if (zo >= zs && yr < ny &&
-            check_range(err, (ty + 2 * ry) * PW + 4 * qx + 2 * rx + 3, 0, PH * PW,
-                        kChkSmoothSmem)) {
-            float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            for (int dz = 0; dz < WZ; ++dz) {
-                const int qz = zo - rz + dz;
-                if (qz < 0 || qz >= nz)
-                    continue;  // zero plane
-                const float *Pz = ring + ((qz - (zs - rz)) % WZ) * PH * PW;
-                for (int dy = 0; dy < WY; ++dy) {
-                    // row ty + dy of the slot; the window's last read is
-                    // column 4 qx + 2 rx + 3 < PW
-                    const float *row = Pz + (ty + dy) * PW + 4 * qx;
-                    const float *wrow = Ws + (dz * WY + dy) * WX;
-                    float v0 = row[0], v1 = row[1], v2 = row[2];
-                    for (int dx = 0; dx < WX; ++dx) {
-                        const float v3 = row[dx + 3];
-                        const float wk = wrow[dx];
-                        a[0] = __fmaf_rn(wk, v0, a[0]);
-                        a[1] = __fmaf_rn(wk, v1, a[1]);
-                        a[2] = __fmaf_rn(wk, v2, a[2]);
-                        a[3] = __fmaf_rn(wk, v3, a[3]);
-                        v0 = v1;
-                        v1 = v2;
-                        v2 = v3;
-                    }
-                }
-            }
-            float d[4] = {wsum, wsum, wsum, wsum};
-            if (!(xy_inside && zo - rz >= 0 && zo + rz < nz)) {
-                // near a face: the weight of the in-cube taps only
-                d[0] = d[1] = d[2] = d[3] = 0.0f;
-                for (int dz = 0; dz < WZ; ++dz) {
-                    const int qz = zo - rz + dz;
-                    if (qz < 0 || qz >= nz)
-                        continue;
-                    for (int dy = 0; dy < WY; ++dy) {
-                        const int qy = yr - ry + dy;
-                        if (qy < 0 || qy >= ny)
-                            continue;
-                        const float *wrow = Ws + (dz * WY + dy) * WX;
-                        for (int dx = 0; dx < WX; ++dx) {
-                            const int gx = xq - rx + dx;
-#pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                if (gx + j >= 0 && gx + j < nx)
-                                    d[j] = __fadd_rn(d[j], wrow[dx]);
-                        }
-                    }
-                }
-            }
-            float *dst = out + (static_cast<int64_t>(zo) * ny + yr) * nx;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (xq + j < nx &&
-                    check_range(err, dst + xq + j - out, 0, static_cast<int64_t>(nz) * ny * nx,
-                                kChkSmoothStore))
-                    dst[xq + j] = __fdiv_rn(a[j], d[j]);
-        }
-        __syncthreads();  // the ring slot of plane zi - 2 rz is refilled next
-    }
-}
-
 template <int RZ>
 cudaError_t sep_launch(const float *in, float *out, int nx, int ny, int nz, const SepWeights &w,
                        int zc, int *err, cudaStream_t stream)
@@ -485,7 +367,8 @@ cudaError_t sep_launch(const float *in, float *out, int nx, int ny, int nz, cons
     const int tiles_z = (nz + zc - 1) / zc;
     const size_t smem = static_cast<size_t>((SY + 2 * w.ry) * (SX + 2 * w.rx + 4) +
                                             (SY + 2 * w.ry) * SX) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(smooth_sep<RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(smooth_sep<RZ>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess)
         return e;
@@ -580,13 +463,6 @@ cudaError_t launch_smooth_sep_tma(const CUtensorMap &tmap, float *out, int nx, i
                                                                      w, hx, err, stream);
 }
 
-size_t smooth_direct_smem(int rx, int ry, int rz)
-{
-    const size_t wts = static_cast<size_t>(2 * rx + 1) * (2 * ry + 1) * (2 * rz + 1);
-    const size_t ring = static_cast<size_t>(2 * rz + 1) * (SY + 2 * ry) * (SX + 2 * rx + 4);
-    return (wts + ring) * sizeof(float);
-}
-
 cudaError_t launch_smooth_sep(const float *in, float *out, int nx, int ny, int nz,
                               const SepWeights &w, int *err, cudaStream_t stream)
 {
@@ -596,23 +472,6 @@ cudaError_t launch_smooth_sep(const float *in, float *out, int nx, int ny, int n
     const int zc = nz < 64 ? nz : 64;
     return SepTable<0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12>::run(w.rz, in, out, nx, ny, nz, w,
                                                                   zc, err, stream);
-}
-
-cudaError_t launch_smooth_direct(const float *in, float *out, int nx, int ny, int nz,
-                                 const float *W, int rx, int ry, int rz, float wsum, int *err,
-                                 cudaStream_t stream)
-{
-    const size_t smem = smooth_direct_smem(rx, ry, rz);
-    cudaError_t e = cudaFuncSetAttribute(smooth_direct, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess)
-        return e;
-    const int tiles_x = (nx + SX - 1) / SX, tiles_y = (ny + SY - 1) / SY;
-    const int zc = nz < 32 ? nz : 32;
-    const int tiles_z = (nz + zc - 1) / zc;
-    smooth_direct<<<tiles_x * tiles_y * tiles_z, kSmThreads, smem, stream>>>(
-        in, out, nx, ny, nz, tiles_x, tiles_y, zc, W, rx, ry, rz, wsum, err);
-    return cudaGetLastError();
 }
 
 }  // namespace afd

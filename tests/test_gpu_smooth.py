@@ -82,16 +82,38 @@ def test_gauss_axis_aligned_matches_oracle(afd, ctx, shape, fwhm):
     assert np.array_equal(gpu_gauss(afd, ctx, cube, fwhm, (0.0, 0.0, 0.0)), got)
 
 
-@pytest.mark.parametrize("shape", [(7, 9, 13), (20, 17, 70), (12, 30, 33)])
+# (6, 6, 6) rotated has a 17^3 kernel: its ring of 32-row planes does not fit
+# in shared memory and the 16-row direct kernel runs instead.
+@pytest.mark.parametrize("shape", [(7, 9, 13), (20, 17, 70), (12, 30, 33), (9, 70, 140)])
 @pytest.mark.parametrize("fwhm,angles", [((3.0, 5.0, 2.0), (20.0, 30.0, 40.0)),
                                          ((4.0, 2.0, 2.0), (0.0, 0.0, 35.0)),
-                                         ((2.0, 2.0, 3.0), (60.0, -10.0, 0.0))])
+                                         ((2.0, 2.0, 3.0), (60.0, -10.0, 0.0)),
+                                         ((6.0, 6.0, 6.0), (10.0, 20.0, 30.0))])
 def test_gauss_rotated_matches_oracle(afd, ctx, shape, fwhm, angles):
     rng = np.random.default_rng(sum(shape) + int(sum(angles)))
     cube = rng.standard_normal(shape).astype(np.float32)
     w = oracle.gauss_weights(fwhm, angles)
     got = gpu_gauss(afd, ctx, cube, fwhm, angles)
     assert_close(got, cube, w, w.size)
+
+
+@pytest.mark.parametrize("fwhm", [(3.0, 5.0, 2.0), (2.0, 2.0, 3.0)])
+def test_gauss_rotated_nan_stays_in_window(afd, ctx, fwhm):
+    # a blanked (NaN) voxel reaches exactly the voxels whose window holds it;
+    # the x taps that pad a kernel row to a multiple of four take no part
+    rng = np.random.default_rng(11)
+    cube = rng.standard_normal((10, 40, 90)).astype(np.float32)
+    for z, y, x in [(4, 20, 45), (0, 0, 0), (9, 39, 89), (5, 3, 70)]:
+        cube[z, y, x] = np.nan
+    angles = (25.0, 0.0, 40.0)
+    w = oracle.gauss_weights(fwhm, angles)
+    got = gpu_gauss(afd, ctx, cube, fwhm, angles)
+    ref = oracle.smooth(cube, w)
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    fin = ~np.isnan(ref)
+    clean = np.where(np.isnan(cube), 0.0, cube)
+    bound = (w.size + 8) * U * oracle.smooth(np.abs(clean), w) + 1e-30
+    assert (np.abs(got[fin].astype(np.float64) - ref[fin]) <= bound[fin]).all()
 
 
 @pytest.mark.parametrize("shape", [(9, 20, 64), (70, 33, 132), (5, 3, 4)])
