@@ -214,6 +214,8 @@ __device__ __forceinline__ void chunk_planes(int tz, int zc, int nz, int &z0, in
 // each other.
 template <int S>
 struct OneCube {
+    // one cube: the fixed thread mapping (its code path stays the plain one)
+    static constexpr bool kRemap = false;
     const void *map;
     typename Store<S>::T *out;
     int nx, ny, nz, tiles_x, txy;
@@ -253,6 +255,8 @@ struct OneCube {
 // round-robin.
 template <int S>
 struct ManyCubes {
+    // ragged cutouts: narrow edge tiles remapped, idle warps skip (stream_body)
+    static constexpr bool kRemap = true;
     const BatchDesc *desc;
     const int2 *list;
     const int2 *roles;
@@ -459,20 +463,27 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
     }
 
     // ---------------- consumers ----------------
-    const int qx = threadIdx.x & 15;
-    const int ry = threadIdx.x >> 4;
-    const int r0 = 1 + 2 * ry;                 // slot row of the first row
-    int cen0 = r0 * SL::PX + SL::HX + 4 * qx;  // quad of row 0 in a slot (elements)
-    int cen1 = cen0 + SL::PX;                  // quad of row 1
+    // Thread mapping: 16 quads x 16 row pairs.  With Src::kRemap (many
+    // ragged cubes), per tile: a tile whose columns inside the cube fit in
+    // its left half (the last tile column of a cube that ends there) takes
+    // 8 quads x 32 row pairs, which puts all of its rows in warps 0-3; and a
+    // warp whose rows all lie past the tile or past the cube keeps the slot
+    // protocol (the same waits and releases) but skips the arithmetic.
+    // Every active thread computes the same 4 x 2 block with the same
+    // arithmetic under either mapping.
+    const int qx_d = threadIdx.x & 15;
+    const int ry_d = threadIdx.x >> 4;
+    int cen0_d = (1 + 2 * ry_d) * SL::PX + SL::HX + 4 * qx_d;  // quad of row 0 in a slot
+    int cen1_d = cen0_d + SL::PX;                               // quad of row 1
     // the block reads slot elements [cen0 - PX, cen1 + PX + 4); a thread
     // that would leave the slot (checked builds) reads a safe block instead
     // and stores nothing
-    const bool slot_ok =
-        check_range(err, cen0 - SL::PX, 0, SL::PX * PY, kChkStreamSlot) &&
-        check_range(err, cen1 + SL::PX + 3, 0, SL::PX * PY, kChkStreamSlot);
-    if (!slot_ok) {
-        cen0 = SL::PX + SL::HX;
-        cen1 = cen0 + SL::PX;
+    const bool slot_ok_d =
+        check_range(err, cen0_d - SL::PX, 0, SL::PX * PY, kChkStreamSlot) &&
+        check_range(err, cen1_d + SL::PX + 3, 0, SL::PX * PY, kChkStreamSlot);
+    if (!slot_ok_d) {
+        cen0_d = SL::PX + SL::HX;
+        cen1_d = cen0_d + SL::PX;
     }
     uint32_t kk = 0;
 
@@ -486,6 +497,25 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
         TileInfo<S> tc;
         src.tile(t, tc);
         const int nx = tc.nx, ny = tc.ny, nz = tc.nz;
+        int qx = qx_d, ry = ry_d, cen0 = cen0_d, cen1 = cen1_d;
+        bool slot_ok = slot_ok_d, idle = false;
+        if constexpr (Src::kRemap) {
+            const bool narrow = nx - tc.x0 <= TX / 2;
+            // warp-uniform: the warp's first row is past the tile or the cube
+            idle = (narrow && warp >= NCW / 2) || tc.y0 + (narrow ? 8 : 4) * warp >= ny;
+            if (narrow && !idle) {
+                qx = threadIdx.x & 7;
+                ry = threadIdx.x >> 3;
+                cen0 = (1 + 2 * ry) * SL::PX + SL::HX + 4 * qx;
+                cen1 = cen0 + SL::PX;
+                slot_ok = check_range(err, cen0 - SL::PX, 0, SL::PX * PY, kChkStreamSlot) &&
+                          check_range(err, cen1 + SL::PX + 3, 0, SL::PX * PY, kChkStreamSlot);
+                if (!slot_ok) {
+                    cen0 = SL::PX + SL::HX;
+                    cen1 = cen0 + SL::PX;
+                }
+            }
+        }
         Packed k;
         k.ax = f2_pack(tc.k.ax, tc.k.ax);
         k.ay = f2_pack(tc.k.ay, tc.k.ay);
@@ -523,6 +553,27 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
         if (lane == 0)                                                                   \
             mbar_arrive(&empty[(r) & (NSLOT - 1)]);                                      \
     } while (0)
+
+        if (idle) {
+            // every plane of the chunk: wait for it, release it, in the
+            // order of the arithmetic path below
+            if (tc.z0 > 0) {
+                WAIT_FULL(RING(tc.z0 - 1));
+                WAIT_FULL(RING(tc.z0));
+                RELEASE(RING(tc.z0 - 1));
+            } else {
+                WAIT_FULL(RING(tc.z0));
+            }
+            for (int z = tc.z0; z < tc.z1; ++z) {
+                if (z + 1 < nz)
+                    WAIT_FULL(RING(z + 1));
+                RELEASE(RING(z));
+            }
+            if (tc.z1 < nz)
+                RELEASE(RING(tc.z1));
+            kk = kbase + static_cast<uint32_t>(tc.np);
+            continue;
+        }
 
         Q cur0, cur1, fb0, fb1;  // current plane and the flux through its lower z face
         {

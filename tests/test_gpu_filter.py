@@ -71,6 +71,8 @@ def test_single_iteration_error(afd, ctx, cond):
 SHAPES = [  # (nz, ny, nx): several tiles and a ragged tail on every axis
     (1, 1, 1), (1, 1, 4), (3, 1, 8), (2, 3, 5), (5, 17, 33), (9, 35, 132), (37, 19, 68),
     (12, 16, 64), (17, 40, 196),
+    # last tile column 28 and 32 wide (the 8-quad mapping), last tile row 6 and 13 high
+    (6, 70, 92), (5, 45, 160),
 ]
 
 
