@@ -169,7 +169,7 @@ size_t smooth_direct_smem(int rx, int ry, int rz);  // bytes of shared memory it
 // cubes.  tmap: 3-D float32 map over the input with the box of
 // smooth_tma_box (x halo hx, a multiple of 4 >= rx).
 void smooth_tma_box(int rx, int ry, int *box_w, int *box_h, int *hx);
-size_t smooth_tma_smem(int ry, int hx);
+size_t smooth_tma_smem(int ry, int hx, int rz);
 cudaError_t launch_smooth_sep_tma(const CUtensorMap &tmap, float *out, int nx, int ny, int nz,
                                   const SepWeights &w, int hx, int *err, cudaStream_t stream);
 // F diagnostic sums over the ROI box roi = {x0, x1, y0, y1, z0, z1} of cubes
