@@ -106,6 +106,46 @@ __device__ __forceinline__ void sep_y_quad(const float *__restrict__ P, int pp,
     d[1] = make_float2(a2, a3);
 }
 
+// y sums of two rows r, r + 1 (the products and sums of sep_y_quad, k
+// ascending for each): every loaded row feeds both, with weights k and k - 1
+__device__ __forceinline__ void sep_y_pair(const float *__restrict__ P, int pp,
+                                           float *__restrict__ Y, int yp, int r, int c,
+                                           const SepWeights &w)
+{
+    const float *p = P + r * pp + c;
+    const int ry2 = 2 * w.ry;
+    float4 v = *reinterpret_cast<const float4 *>(p);
+    float wp = w.wy[0];
+    float a0 = __fmaf_rn(wp, v.x, 0.0f), a1 = __fmaf_rn(wp, v.y, 0.0f);
+    float a2 = __fmaf_rn(wp, v.z, 0.0f), a3 = __fmaf_rn(wp, v.w, 0.0f);
+    float b0 = 0.0f, b1 = 0.0f, b2 = 0.0f, b3 = 0.0f;
+#pragma unroll 2
+    for (int i = 1; i <= ry2; ++i) {  // row r + i: tap i of row r, tap i - 1 of row r + 1
+        v = *reinterpret_cast<const float4 *>(p + i * pp);
+        const float wc = w.wy[i];
+        a0 = __fmaf_rn(wc, v.x, a0);
+        a1 = __fmaf_rn(wc, v.y, a1);
+        a2 = __fmaf_rn(wc, v.z, a2);
+        a3 = __fmaf_rn(wc, v.w, a3);
+        b0 = __fmaf_rn(wp, v.x, b0);
+        b1 = __fmaf_rn(wp, v.y, b1);
+        b2 = __fmaf_rn(wp, v.z, b2);
+        b3 = __fmaf_rn(wp, v.w, b3);
+        wp = wc;
+    }
+    v = *reinterpret_cast<const float4 *>(p + (ry2 + 1) * pp);  // tap 2 ry of row r + 1
+    b0 = __fmaf_rn(wp, v.x, b0);
+    b1 = __fmaf_rn(wp, v.y, b1);
+    b2 = __fmaf_rn(wp, v.z, b2);
+    b3 = __fmaf_rn(wp, v.w, b3);
+    float2 *d = reinterpret_cast<float2 *>(Y + r * yp + c);
+    d[0] = make_float2(a0, a1);
+    d[1] = make_float2(a2, a3);
+    d = reinterpret_cast<float2 *>(Y + (r + 1) * yp + c);
+    d[0] = make_float2(b0, b1);
+    d[1] = make_float2(b2, b3);
+}
+
 // x sums of the thread's quad: a_j = sum_k wx[k] row[j + k], k ascending;
 // row points at the first tap of voxel 0 (2 rx + 4 floats are read)
 __device__ __forceinline__ void sep_x_quad(const float *__restrict__ row, const SepWeights &w,
@@ -273,15 +313,20 @@ __global__ void __launch_bounds__(kSmThreads, 1)
             }
         }
         __syncthreads();
-        // ---- 2: y sums of the tile's rows over every column of the plane:
-        // the quad under the tile, then the x halo's 16 x hx/2 quads
-        if (check_range(err, (ty + 2 * ry) * SW + hx + 4 * qx + 3, 0, SH * SW, kChkSmoothSmem))
-            sep_y_quad(P, SW, Y, YP, ty, hx + 4 * qx, w);
-        for (int h = tid; h < nhq; h += kSmThreads) {
-            const int r = h & 15, hq = h >> 4;  // hq < hx/4: left, else right
-            const int c = 4 * hq + (hq < hx / 4 ? 0 : SX);
-            if (check_range(err, (r + 2 * ry) * SW + c + 3, 0, SH * SW, kChkSmoothSmem))
-                sep_y_quad(P, SW, Y, YP, r, c, w);
+        // ---- 2: y sums of the tile's rows over every column of the plane,
+        // by row pairs: threads 0-127 the 8 x 16 under the tile, 128-255
+        // the x halo's 8 x hx/2
+        if (tid < kSmThreads / 2) {
+            const int r = 2 * (tid >> 4), c = hx + 4 * qx;
+            if (check_range(err, (r + 1 + 2 * ry) * SW + c + 3, 0, SH * SW, kChkSmoothSmem))
+                sep_y_pair(P, SW, Y, YP, r, c, w);
+        } else {
+            for (int h = tid - kSmThreads / 2; h < nhq / 2; h += kSmThreads / 2) {
+                const int r = 2 * (h & 7), hq = h >> 3;  // hq < hx/4: left, else right
+                const int c = 4 * hq + (hq < hx / 4 ? 0 : SX);
+                if (check_range(err, (r + 1 + 2 * ry) * SW + c + 3, 0, SH * SW, kChkSmoothSmem))
+                    sep_y_pair(P, SW, Y, YP, r, c, w);
+            }
         }
         __syncthreads();
         // ---- 3: x sums of the thread's quad, into the z ring
@@ -410,16 +455,19 @@ __global__ void __launch_bounds__(kSmTmaThreads, RZ <= 4 ? 3 : 2)
             if (waiting && !mbar_wait(&full[slot], (j / kSmSlots) & 1u, err, kErrWaitFull))
                 waiting = false;
             const float *S = reinterpret_cast<const float *>(smem + slot * slot_stride);
-            if (cons) {
-                const int c = hx + 4 * qx;  // the quad under the tile
-                if (check_range(err, (ty + 2 * ry) * SW + c + 3, 0, SH * SW, kChkSmoothSmem))
-                    sep_y_quad(S, SW, Y, YP, ty, c, w);
-            } else {
-                for (int h = lane; h < nhq; h += 32) {
-                    const int r = h & 15, hq = h >> 4;  // hq < hx/4: left, else right
+            // by row pairs: warps 0-3 the 8 x 16 under the tile, warp 8 the
+            // x halo's 8 x hx/2 (warps 4-7 have none)
+            if (tid < kSmThreads / 2) {
+                const int r = 2 * (tid >> 4), c = hx + 4 * qx;
+                if (check_range(err, (r + 1 + 2 * ry) * SW + c + 3, 0, SH * SW, kChkSmoothSmem))
+                    sep_y_pair(S, SW, Y, YP, r, c, w);
+            } else if (!cons) {
+                for (int h = lane; h < nhq / 2; h += 32) {
+                    const int r = 2 * (h & 7), hq = h >> 3;  // hq < hx/4: left, else right
                     const int c = 4 * hq + (hq < hx / 4 ? 0 : SX);
-                    if (check_range(err, (r + 2 * ry) * SW + c + 3, 0, SH * SW, kChkSmoothSmem))
-                        sep_y_quad(S, SW, Y, YP, r, c, w);
+                    if (check_range(err, (r + 1 + 2 * ry) * SW + c + 3, 0, SH * SW,
+                                    kChkSmoothSmem))
+                        sep_y_pair(S, SW, Y, YP, r, c, w);
                 }
             }
             __syncwarp();
