@@ -167,11 +167,12 @@ __device__ __forceinline__ void sep_x_quad(const float *__restrict__ row, const 
     }
 }
 
-// The z window of the thread's quad: the xy sums of the last 2 RZ + 1 planes.
-// Small windows live in registers (shifted by one per plane); from
-// kSepSmemRingRz on, in shared memory, one float4 per plane and thread in
-// slots taken modulo 2 RZ + 1, so that registers stay few.  Either way the
-// output sums its planes oldest first.
+// The z window of the thread's quad: the xy sums of the last planes.  Small
+// windows live in registers (shifted by one per plane); from kSepSmemRingRz
+// on, in shared memory, one float4 per plane and thread in slots taken
+// modulo 2 RZ + 1, so that registers stay few.  step() takes plane zi's sums
+// and hands each output plane zo >= zs that is complete to put(zo, sums);
+// every output sums its planes oldest first.
 constexpr int kSepSmemRingRz = 3;
 
 template <int RZ, bool SMEM = (RZ >= kSepSmemRingRz)>
@@ -188,8 +189,9 @@ struct SepRing<RZ, false> {
             for (int j = 0; j < 4; ++j)
                 v[m][j] = 0.0f;
     }
-    // the xy sums of plane zi (planes arrive in order, one push each)
-    __device__ __forceinline__ void push(int, const float (&c)[4])
+    template <class Put>
+    __device__ __forceinline__ void step(int zi, int zs, int, const float (&c)[4],
+                                         const SepWeights &w, Put &&put)
     {
 #pragma unroll
         for (int m = 0; m < 2 * RZ; ++m)
@@ -199,10 +201,10 @@ struct SepRing<RZ, false> {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             v[2 * RZ][j] = c[j];
-    }
-    // z sums of output plane zo = (last plane pushed) - RZ
-    __device__ __forceinline__ void zsum(int, const SepWeights &w, float (&s)[4]) const
-    {
+        const int zo = zi - RZ;
+        if (zo < zs)
+            return;
+        float s[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             s[j] = 0.0f;
@@ -210,9 +212,14 @@ struct SepRing<RZ, false> {
             for (int k = 0; k <= 2 * RZ; ++k)
                 s[j] = __fmaf_rn(w.wz[k], v[k][j], s[j]);
         }
+        put(zo, s);
     }
 };
 
+// Output planes leave in pairs (zo - 1, zo), formed before plane zi = zo + RZ
+// is stored: one pass over the 2 RZ + 1 stored planes zi - 2 RZ - 1 .. zi - 1
+// and the new plane's sums in registers serves both, half the loads of two
+// single sums.  A chunk with an odd number of outputs ends with a single one.
 template <int RZ>
 struct SepRing<RZ, true> {
     static constexpr int W = 2 * RZ + 1;
@@ -221,24 +228,49 @@ struct SepRing<RZ, true> {
     __device__ __forceinline__ SepRing(float4 *ring, int nthreads) : base(ring), stride(nthreads)
     {
     }
-    __device__ __forceinline__ void push(int zi, const float (&c)[4])
+    template <class Put>
+    __device__ __forceinline__ void step(int zi, int zs, int ze, const float (&c)[4],
+                                         const SepWeights &w, Put &&put)
     {
-        base[((zi + W) % W) * stride] = make_float4(c[0], c[1], c[2], c[3]);  // zi >= -RZ
-    }
-    __device__ __forceinline__ void zsum(int zo, const SepWeights &w, float (&s)[4]) const
-    {
-        s[0] = s[1] = s[2] = s[3] = 0.0f;
-        int m = (zo - RZ + W) % W;  // the oldest plane, zo - RZ >= -RZ
+        const int zo = zi - RZ, q = zo - zs;
+        if (q >= 0 && ((q & 1) || zo == ze - 1)) {
+            const bool pair = (q & 1) != 0;  // the same for the whole CTA
+            float a[4] = {0.0f, 0.0f, 0.0f, 0.0f}, b[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            int m = (zi - 2 * RZ - 1 + W) % W;  // plane zo - 1 - RZ >= -RZ - 1
+            if (pair) {  // tap 0 of zo - 1
+                const float4 v = base[m * stride];
+                const float wk = w.wz[0];
+                a[0] = __fmaf_rn(wk, v.x, a[0]);
+                a[1] = __fmaf_rn(wk, v.y, a[1]);
+                a[2] = __fmaf_rn(wk, v.z, a[2]);
+                a[3] = __fmaf_rn(wk, v.w, a[3]);
+            }
 #pragma unroll
-        for (int k = 0; k <= 2 * RZ; ++k) {
-            const float4 v = base[m * stride];
-            const float wk = w.wz[k];
-            s[0] = __fmaf_rn(wk, v.x, s[0]);
-            s[1] = __fmaf_rn(wk, v.y, s[1]);
-            s[2] = __fmaf_rn(wk, v.z, s[2]);
-            s[3] = __fmaf_rn(wk, v.w, s[3]);
-            m = m + 1 == W ? 0 : m + 1;
+            for (int i = 1; i <= 2 * RZ; ++i) {  // plane zo - 1 - RZ + i
+                m = m + 1 == W ? 0 : m + 1;
+                const float4 v = base[m * stride];
+                if (pair) {  // tap i of zo - 1
+                    const float wa = w.wz[i];
+                    a[0] = __fmaf_rn(wa, v.x, a[0]);
+                    a[1] = __fmaf_rn(wa, v.y, a[1]);
+                    a[2] = __fmaf_rn(wa, v.z, a[2]);
+                    a[3] = __fmaf_rn(wa, v.w, a[3]);
+                }
+                const float wb = w.wz[i - 1];  // tap i - 1 of zo
+                b[0] = __fmaf_rn(wb, v.x, b[0]);
+                b[1] = __fmaf_rn(wb, v.y, b[1]);
+                b[2] = __fmaf_rn(wb, v.z, b[2]);
+                b[3] = __fmaf_rn(wb, v.w, b[3]);
+            }
+            const float wl = w.wz[2 * RZ];  // tap 2 RZ of zo: plane zi
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                b[j] = __fmaf_rn(wl, c[j], b[j]);
+            if (pair)
+                put(zo - 1, a);
+            put(zo, b);
         }
+        base[((zi + W) % W) * stride] = make_float4(c[0], c[1], c[2], c[3]);  // zi >= -RZ
     }
 };
 
@@ -333,12 +365,11 @@ __global__ void __launch_bounds__(kSmThreads, 1)
         float c4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         if (x_ok)
             sep_x_quad(Y + ty * YP + (hx - rx) + 4 * qx, w, c4);
-        ring.push(zi, c4);
-        // ---- 4: the output plane zo = zi - RZ: z sum, normalise, store
-        const int zo = zi - RZ;
-        if (zo >= zs && yr < ny) {
-            float sz[4], o[4];
-            ring.zsum(zo, w, sz);
+        // ---- 4: z sums of the output planes now complete; normalise, store
+        ring.step(zi, zs, ze, c4, w, [&](int zo, const float (&sz)[4]) {
+            if (yr >= ny)
+                return;
+            float o[4];
             sep_norm(sz, inv_xy, sep_inv_z<RZ>(w, zo, nz, inv_zf), o);
             float *dst = out + (static_cast<int64_t>(zo) * ny + yr) * nx;
 #pragma unroll
@@ -347,7 +378,7 @@ __global__ void __launch_bounds__(kSmThreads, 1)
                     check_range(err, dst + xq + j - out, 0, static_cast<int64_t>(nz) * ny * nx,
                                 kChkSmoothStore))
                     dst[xq + j] = o[j];
-        }
+        });
         // the next iteration rewrites P right away: every read of P happened
         // before the second barrier above; it rewrites Y only after its first
         // barrier, which follows these reads of Y
@@ -482,17 +513,16 @@ __global__ void __launch_bounds__(kSmTmaThreads, RZ <= 4 ? 3 : 2)
         float c4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         if (have && x_ok)
             sep_x_quad(Y + ty * YP + (hx - rx) + 4 * qx, w, c4);
-        ring.push(zi, c4);
-        const int zo = zi - RZ;
-        if (zo >= zs && yr < ny && xq < nx) {
-            float sz[4], o[4];
-            ring.zsum(zo, w, sz);
+        ring.step(zi, zs, ze, c4, w, [&](int zo, const float (&sz)[4]) {
+            if (yr >= ny || xq >= nx)
+                return;
+            float o[4];
             sep_norm(sz, inv_xy, sep_inv_z<RZ>(w, zo, nz, inv_zf), o);
             // nx % 4 == 0 and xq % 4 == 0: the quad is inside the row
             const int64_t oi = (static_cast<int64_t>(zo) * ny + yr) * nx + xq;
             if (check_range(err, oi, 0, static_cast<int64_t>(nz) * ny * nx - 3, kChkSmoothStore))
                 *reinterpret_cast<float4 *>(out + oi) = make_float4(o[0], o[1], o[2], o[3]);
-        }
+        });
     }
 }
 
