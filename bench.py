@@ -58,9 +58,11 @@ def parse_args():
     ap.add_argument("--impl", choices=["afd", "reference"], default="afd")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--lines", default="paper,diagnostics,smoothing,precision,batch,serving",
+    ap.add_argument("--lines",
+                    default="paper,diagnostics,smoothing,precision,slabs,batch,serving",
                     help="extra lines measured after the headline (N=1 only): any of "
-                         "paper, diagnostics, smoothing, precision, batch, serving, or 'none'")
+                         "paper, diagnostics, smoothing, precision, slabs, batch, serving, or "
+                         "'none'")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="arrival window per request rate of the serving line")
     return ap.parse_args()
@@ -413,6 +415,58 @@ def line_smoothing(afd, ctx):
                               "note": "N = 1.4e8, other hardware; context only"}}
 
 
+def line_slabs(afd, ctx, cube, sig):
+    """A cube filtered out of host memory through a small device budget
+    (afd_filter_slabs): z-slabs with halo planes, rounds of `halo`
+    iterations, copies overlapped with the passes.  The cube is the headline
+    cube stacked four times along z (512 x 512 x 1024, 1 GiB); host to host,
+    pinned buffers.  Context: the same cube through afd_filter_host (whole
+    cube on the device)."""
+    import numpy as np
+    import torch
+    big = np.ascontiguousarray(np.tile(cube, (4, 1, 1)))
+    nz, ny, nx = big.shape
+    plane = nx * ny * 4
+    n_vox = big.size
+    K = K_SIGMA * sig
+    h_in = torch.from_numpy(big).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    h_tmp = torch.empty_like(h_in).pin_memory()
+    rows = []
+    for slab_nz, halo in ((64, 10), (64, 25), (128, 25), (128, 50)):
+        run = lambda: afd.afd_filter_slabs(ctx, h_in, h_out, K, DT, N_ITER, COND, None,
+                                           slab_nz, halo, h_tmp)
+        run()
+        secs = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            run()
+            secs.append(time.perf_counter() - t0)
+        sec = statistics.median(secs)
+        rounds = -(-N_ITER // halo)
+        slabs = -(-nz // slab_nz)
+        # planes copied in per round: every slab with its ghost planes
+        planes_in = sum(min(nz, z0 + slab_nz + halo) - max(0, z0 - halo)
+                        for z0 in range(0, nz, slab_nz))
+        moved = rounds * (planes_in + nz) * plane
+        rows.append({"slab_nz": slab_nz, "halo": halo, "rounds": rounds, "slabs": slabs,
+                     "device_bytes": 4 * min(nz, slab_nz + 2 * halo) * plane,
+                     "s": sec, "value": n_vox * N_ITER / sec / 1e9,
+                     "host_link_GBs": moved / sec / 1e9})
+    t0 = time.perf_counter()
+    afd.afd_filter_host(ctx, h_in, h_out, K, DT, N_ITER, COND)
+    whole = time.perf_counter() - t0
+    best = max(rows, key=lambda r: r["value"])
+    return {"unit": UNIT, "workload": "the headline cube stacked 4x along z (512x512x1024 "
+            "float32, 1 GiB) in pinned host memory, K = 1.0 sigma, dt = 1/8, 50 rational "
+            "iterations, host to host; device_bytes: the two staging slots (in + out) at "
+            "the largest slab, besides a pass scratch of one slab",
+            "best": {"slab_nz": best["slab_nz"], "halo": best["halo"], "value": best["value"]},
+            "rows": rows,
+            "whole_cube_host": {"s": whole, "value": n_vox * N_ITER / whole / 1e9,
+                                "device_bytes": 3 * n_vox * 4}}
+
+
 def line_batch(afd, ctx):
     """300 galaxy cutouts of uneven size, K_i = 1.5 sigma_i (GPU FP64 noise
     estimate), 20 iterations, one CUDA-graph launch per call; z-chunk picked
@@ -642,6 +696,8 @@ def run_afd(args):
             lines["diagnostics"] = line_diagnostics(afd, ctx, d_in, d_out)
         if "precision" in want:
             lines["precision"] = line_precision(afd, ctx, cube, d_in, d_out, sig)
+        if "slabs" in want:
+            lines["slabs"] = line_slabs(afd, ctx, cube, sig)
         if "batch" in want:
             lines["batch"] = line_batch(afd, ctx)
         if "serving" in want:

@@ -201,6 +201,30 @@ afd_status afd_filter_host_async(afd_ctx *ctx, const float *host_in, float *host
                                  int64_t ny, int64_t nz, const float *spacing, float K, float dt,
                                  int n_iter, afd_conductance cond);
 
+/* afd_filter for a cube larger than the device memory it may use: the cube
+ * stays in HOST memory and passes through the device in z-slabs of slab_nz
+ * planes, in rounds of up to `halo` iterations.  An explicit nearest-
+ * neighbour iteration (Sec. 3.3) moves information one plane per iteration,
+ * so a slab loaded with `halo` extra planes on each side (fewer at the
+ * cube's z faces, which are the true zero-flux faces) and filtered for
+ * `halo` iterations holds the whole cube's result on its own planes: the
+ * result is bit-identical to afd_filter on the whole cube.  Extends the
+ * paper's memory model (Sec. 6: the cube in RAM, two cube-sized buffers in
+ * DRAM) to device memory of 2 x 2 x (slab_nz + 2 halo) planes.
+ *   host_in   the cube (x fastest); unchanged.  Pinned memory lets the copies
+ *             overlap the passes (two staging slots on two copy streams).
+ *   host_out  the result; must not be host_in.
+ *   host_tmp  a cube-sized host buffer, used when n_iter > halo (the rounds
+ *             alternate between it and host_out); may be NULL otherwise.
+ *   slab_nz   >= 1 planes per slab; halo >= 1 iterations per round.
+ * Host traffic per round: the cube in (plus 2 halo planes per slab) and
+ * out.  Synchronous: returns when host_out holds the result.  Returns
+ * AFD_EINVAL for bad arguments (nothing is done), else as afd_sync. */
+afd_status afd_filter_slabs(afd_ctx *ctx, const float *host_in, float *host_out, float *host_tmp,
+                            int64_t nx, int64_t ny, int64_t nz, const float *spacing, float K,
+                            float dt, int n_iter, afd_conductance cond, int64_t slab_nz,
+                            int halo);
+
 /* Round a float32 cube into a 2-byte storage format (precision line): out[i]
  * = RN(in[i] / scale) in float16 or bfloat16, or RN(in[i] * 1024 / scale)
  * as int16 clamped to +-32767; nearest, ties to even.

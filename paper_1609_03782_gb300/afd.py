@@ -52,6 +52,8 @@ def _load():
         "afd_filter_out": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_host": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
         "afd_filter_host_async": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int], c_int),
+        "afd_filter_slabs": ([vp, vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int, i64,
+                              c_int], c_int),
         "afd_filter_rel": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, c_int, c_int, vp], c_int),
         "afd_f_diagnostic": ([vp, vp, vp, vp, i64, i64, i64, vp, ctypes.c_double,
                               ctypes.c_double, ctypes.c_double, ctypes.c_double, vp], c_int),
@@ -383,6 +385,31 @@ def afd_filter_host_async(ctx: Context, host_in: torch.Tensor, host_out: torch.T
     _check(_lib.afd_filter_host_async(ctx.handle, p_in, p_out, nx, ny, nz, _spacing(spacing),
                                       float(K), float(dt), int(n_iter), COND[conductance]),
            "afd_filter_host_async", ctx)
+    return host_out
+
+
+def afd_filter_slabs(ctx: Context, host_in: torch.Tensor, host_out: torch.Tensor, K: float,
+                     dt: float, n_iter: int, conductance: str = "rational", spacing=None,
+                     slab_nz: int = 64, halo: int = 8, host_tmp: torch.Tensor = None
+                     ) -> torch.Tensor:
+    """Filter a float32 CPU cube through the device in z-slabs of slab_nz
+    planes, in rounds of up to `halo` iterations (device memory: four slabs
+    of slab_nz + 2 halo planes); synchronous.  Bit-identical to afd_filter on
+    the whole cube.  host_tmp (a cube-sized CPU tensor) is needed when
+    n_iter > halo; pinned tensors let the copies overlap the passes."""
+    for t in (host_in, host_out) + ((host_tmp,) if host_tmp is not None else ()):
+        if t.dtype != torch.float32 or t.is_cuda:
+            raise ValueError("afd_filter_slabs takes float32 CPU tensors")
+        if t.shape != host_in.shape:
+            raise ValueError("afd_filter_slabs: shapes differ")
+    p_in, nx, ny, nz = _cube_args(host_in)
+    p_out, _, _, _ = _cube_args(host_out)
+    p_tmp = _cube_args(host_tmp)[0] if host_tmp is not None else None
+    _use_current_stream(ctx)
+    _check(_lib.afd_filter_slabs(ctx.handle, p_in, p_out, p_tmp, nx, ny, nz, _spacing(spacing),
+                                 float(K), float(dt), int(n_iter), COND[conductance],
+                                 int(slab_nz), int(halo)),
+           "afd_filter_slabs", ctx)
     return host_out
 
 

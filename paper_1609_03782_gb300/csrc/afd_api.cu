@@ -965,10 +965,14 @@ namespace {
 // copy on its D2H stream, ordered by the slot's events.  A slot's input
 // buffer is refilled only after the passes that read it are done, and its
 // result buffer rewritten only after its copy to the host is done.
-afd_status enqueue_host_filter(afd_ctx *ctx, int slot, const float *host_in, float *host_out,
-                               int64_t nx, int64_t ny, int64_t nz, const float *spacing, float K,
-                               float dt, int n_iter, afd_conductance cond)
+// The copy streams and a staging slot's events, created on first use; the
+// slot's device buffer is two fixed halves (input, then output) of at least
+// `bytes` each.  Fixed halves: a later use of the slot, whatever its size,
+// writes only the input half, which never overlaps the output half that an
+// earlier use's copy back may still be reading.
+afd_status ensure_host_slot(afd_ctx *ctx, int slot, size_t bytes)
 {
+    bytes = (bytes + 255) & ~size_t(255);  // the output half stays 256-byte aligned
     cudaError_t e = cudaSuccess;
     if (!ctx->h2d_stream)
         e = cudaStreamCreateWithFlags(&ctx->h2d_stream, cudaStreamNonBlocking);
@@ -984,7 +988,6 @@ afd_status enqueue_host_filter(afd_ctx *ctx, int slot, const float *host_in, flo
     }
     if (e != cudaSuccess)
         return cuda_fail(ctx, e);
-    const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
     if (s.bytes < 2 * bytes) {
         // the slot's old buffer may still be in use: let all its work finish
         e = cudaEventSynchronize(s.copied_out);
@@ -1003,8 +1006,26 @@ afd_status enqueue_host_filter(afd_ctx *ctx, int slot, const float *host_in, flo
         s.buf = static_cast<float *>(p);
         s.bytes = 2 * bytes;
     }
+    return AFD_OK;
+}
+
+// One cube (or z-slab) through staging slot `slot`: host_in -> device ->
+// n_iter iterations -> planes [oz0, oz1) of the result -> host_out (which
+// points at the destination of plane oz0).  Stream-ordered: the copies run on
+// the copy streams and overlap the other slot's work.
+afd_status enqueue_host_filter(afd_ctx *ctx, int slot, const float *host_in, float *host_out,
+                               int64_t nx, int64_t ny, int64_t nz, const float *spacing, float K,
+                               float dt, int n_iter, afd_conductance cond, int64_t oz0,
+                               int64_t oz1)
+{
+    const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
+    afd_status st0 = ensure_host_slot(ctx, slot, bytes);
+    if (st0 != AFD_OK)
+        return st0;
+    afd_ctx::HostSlot &s = ctx->host_slot[slot];
+    cudaError_t e = cudaSuccess;
     float *d_in = s.buf;
-    float *d_out = s.buf + nx * ny * nz;
+    float *d_out = s.buf + s.bytes / 2 / sizeof(float);  // the output half
     // (waiting on an event that was never recorded returns at once)
     e = cudaStreamWaitEvent(ctx->h2d_stream, s.filtered, 0);
     if (e == cudaSuccess)
@@ -1024,7 +1045,9 @@ afd_status enqueue_host_filter(afd_ctx *ctx, int slot, const float *host_in, flo
     if (e == cudaSuccess)
         e = cudaStreamWaitEvent(ctx->d2h_stream, s.filtered, 0);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(host_out, d_out, bytes, cudaMemcpyDeviceToHost, ctx->d2h_stream);
+        e = cudaMemcpyAsync(host_out, d_out + oz0 * nx * ny,
+                            static_cast<size_t>((oz1 - oz0) * nx * ny) * sizeof(float),
+                            cudaMemcpyDeviceToHost, ctx->d2h_stream);
     if (e == cudaSuccess)
         e = cudaEventRecord(s.copied_out, ctx->d2h_stream);
     return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
@@ -1050,7 +1073,8 @@ afd_status afd_filter_host(afd_ctx *ctx, const float *host_in, float *host_out, 
     afd_status st = set_device(ctx);
     if (st != AFD_OK)
         return st;
-    st = enqueue_host_filter(ctx, 0, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter, cond);
+    st = enqueue_host_filter(ctx, 0, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter, cond,
+                             0, nz);
     if (st != AFD_OK)
         return st;
     return afd_sync(ctx);
@@ -1068,9 +1092,70 @@ afd_status afd_filter_host_async(afd_ctx *ctx, const float *host_in, float *host
         return st;
     const int slot = static_cast<int>(ctx->host_calls & 1ull);
     st = enqueue_host_filter(ctx, slot, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter,
-                             cond);
+                             cond, 0, nz);
     if (st == AFD_OK)
         ctx->host_calls++;
+    return st;
+}
+
+afd_status afd_filter_slabs(afd_ctx *ctx, const float *host_in, float *host_out, float *host_tmp,
+                            int64_t nx, int64_t ny, int64_t nz, const float *spacing, float K,
+                            float dt, int n_iter, afd_conductance cond, int64_t slab_nz, int halo)
+{
+    const afd_host::TraceRange trace_("afd_filter_slabs");
+    if (!host_args_ok(ctx, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter, cond) ||
+        slab_nz < 1 || halo < 1 || host_out == host_in)
+        return AFD_EINVAL;
+    const int rounds = n_iter == 0 ? 1 : (n_iter + halo - 1) / halo;
+    if (rounds > 1 && (!host_tmp || host_tmp == host_in || host_tmp == host_out))
+        return AFD_EINVAL;
+    afd_status st = set_device(ctx);
+    if (st != AFD_OK)
+        return st;
+    const int64_t plane = nx * ny;
+    // both slots and the pass scratch at the largest slab (slab_nz + 2 halo
+    // planes), so that nothing is reallocated between slabs
+    const int64_t max_nz = std::min<int64_t>(nz, slab_nz + 2 * static_cast<int64_t>(halo));
+    const size_t max_bytes = static_cast<size_t>(max_nz * plane) * sizeof(float);
+    for (int slot = 0; slot < 2 && st == AFD_OK; ++slot)
+        st = ensure_host_slot(ctx, slot, max_bytes);
+    if (st == AFD_OK)
+        st = ensure_buffer(ctx, &ctx->scratch, &ctx->scratch_bytes, max_bytes);
+    if (st != AFD_OK)
+        return st;
+    cudaEvent_t round_done = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&round_done, cudaEventDisableTiming);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e);
+    const float *src = host_in;
+    int k = 0;  // slabs enqueued: they alternate between the two slots
+    for (int r = 0; r < rounds && st == AFD_OK; ++r) {
+        const int its = std::min(halo, n_iter - r * halo);  // iterations this round (>= 0)
+        // the last round writes host_out; the rounds before alternate
+        float *dst = ((rounds - 1 - r) % 2 == 0) ? host_out : host_tmp;
+        for (int64_t z0 = 0; z0 < nz && st == AFD_OK; z0 += slab_nz, ++k) {
+            const int64_t z1 = std::min(nz, z0 + slab_nz);
+            // a voxel moves `its` planes in `its` iterations: planes [z0, z1)
+            // of the slab grown by `its` (clamped to the cube, whose faces
+            // are the true zero-flux faces) are the whole cube's
+            const int64_t lo = std::max<int64_t>(0, z0 - its), hi = std::min(nz, z1 + its);
+            st = enqueue_host_filter(ctx, k & 1, src + lo * plane, dst + z0 * plane, nx, ny,
+                                     hi - lo, spacing, K, dt, its, cond, z0 - lo, z1 - lo);
+        }
+        // the next round reads what this round wrote: its copies in wait for
+        // every copy out of this one (in order on the copy-out stream)
+        if (st == AFD_OK) {
+            e = cudaEventRecord(round_done, ctx->d2h_stream);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(ctx->h2d_stream, round_done, 0);
+            if (e != cudaSuccess)
+                st = cuda_fail(ctx, e);
+        }
+        src = dst;
+    }
+    if (st == AFD_OK)
+        st = afd_sync(ctx);
+    cudaEventDestroy(round_done);
     return st;
 }
 

@@ -223,13 +223,17 @@ def test_filter_rel_without_noise_is_identity(afd, ctx):
 
 def test_host_async_sequence(afd, ctx):
     # several cubes in flight through the two staging slots, with different
-    # shapes (a slot grows while the other is busy), parameters and buffer
+    # shapes (a slot grows while the other is busy; a slot takes a small cube
+    # and then a larger one within its capacity, whose copy in must not touch
+    # the small cube's result still being copied out), parameters and buffer
     # kinds; each result equals the same filter on the device, bit for bit
     jobs = [((24, 40, 64), 1.3, 1 / 8, 7, "rational", True),
             ((16, 33, 96), 0.8, 1 / 16, 4, "exponential", True),
             ((40, 64, 128), 2.0, 1 / 8, 3, "rational", False),
             ((24, 40, 64), 1.1, 0.1, 1, "exponential", True),
-            ((9, 20, 36), 1.5, 1 / 8, 5, "rational", False)]
+            ((9, 20, 36), 1.5, 1 / 8, 5, "rational", True),
+            ((8, 16, 32), 1.2, 1 / 8, 2, "rational", True),
+            ((20, 40, 64), 0.9, 1 / 8, 6, "exponential", True)]
     hosts, refs = [], []
     for i, (shape, K, dt, n, cond, pinned) in enumerate(jobs):
         cube = synth.cutout(shape, 300 + i)
