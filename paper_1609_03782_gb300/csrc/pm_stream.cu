@@ -464,13 +464,15 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
 
     // ---------------- consumers ----------------
     // Thread mapping: 16 quads x 16 row pairs.  With Src::kRemap (many
-    // ragged cubes), per tile: a tile whose columns inside the cube fit in
-    // its left half (the last tile column of a cube that ends there) takes
-    // 8 quads x 32 row pairs, which puts all of its rows in warps 0-3; and a
-    // warp whose rows all lie past the tile or past the cube keeps the slot
+    // ragged cubes), per tile: a tile with only w < 64 columns inside the
+    // cube (the last tile column of a cube that ends there) takes nq =
+    // ceil(w / 4) quads per row pair, thread t the quad t % nq of row pair
+    // t / nq, so its 16 row pairs fill the first 16 nq threads; and a warp
+    // whose rows all lie past the tile or past the cube keeps the slot
     // protocol (the same waits and releases) but skips the arithmetic.
-    // Every active thread computes the same 4 x 2 block with the same
-    // arithmetic under either mapping.
+    // Lanes of a working warp past the tile's last row pair compute on a
+    // safe block and store nothing.  Every active thread computes the same
+    // 4 x 2 block with the same arithmetic under any mapping.
     const int qx_d = threadIdx.x & 15;
     const int ry_d = threadIdx.x >> 4;
     int cen0_d = (1 + 2 * ry_d) * SL::PX + SL::HX + 4 * qx_d;  // quad of row 0 in a slot
@@ -500,20 +502,31 @@ __device__ __forceinline__ void stream_body(const Src &src, int64_t ntiles, int 
         int qx = qx_d, ry = ry_d, cen0 = cen0_d, cen1 = cen1_d;
         bool slot_ok = slot_ok_d, idle = false;
         if constexpr (Src::kRemap) {
-            const bool narrow = nx - tc.x0 <= TX / 2;
-            // warp-uniform: the warp's first row is past the tile or the cube
-            idle = (narrow && warp >= NCW / 2) || tc.y0 + (narrow ? 8 : 4) * warp >= ny;
-            if (narrow && !idle) {
-                qx = threadIdx.x & 7;
-                ry = threadIdx.x >> 3;
-                cen0 = (1 + 2 * ry) * SL::PX + SL::HX + 4 * qx;
-                cen1 = cen0 + SL::PX;
-                slot_ok = check_range(err, cen0 - SL::PX, 0, SL::PX * PY, kChkStreamSlot) &&
-                          check_range(err, cen1 + SL::PX + 3, 0, SL::PX * PY, kChkStreamSlot);
-                if (!slot_ok) {
-                    cen0 = SL::PX + SL::HX;
+            const int wq = (nx - tc.x0 + 3) >> 2;  // quads inside the cube
+            if (wq < TX / 4) {
+                const int p_first = (32 * warp) / wq;  // the warp's first row pair
+                // warp-uniform: the warp's first row is past the tile or the cube
+                idle = p_first >= TY / 2 || tc.y0 + 2 * p_first >= ny;
+                if (!idle) {
+                    const int t = threadIdx.x;
+                    ry = t / wq;
+                    qx = t - ry * wq;
+                    const bool lane_on = ry < TY / 2;
+                    if (!lane_on)
+                        ry = qx = 0;
+                    cen0 = (1 + 2 * ry) * SL::PX + SL::HX + 4 * qx;
                     cen1 = cen0 + SL::PX;
+                    slot_ok =
+                        lane_on &&
+                        check_range(err, cen0 - SL::PX, 0, SL::PX * PY, kChkStreamSlot) &&
+                        check_range(err, cen1 + SL::PX + 3, 0, SL::PX * PY, kChkStreamSlot);
+                    if (!slot_ok) {
+                        cen0 = SL::PX + SL::HX;
+                        cen1 = cen0 + SL::PX;
+                    }
                 }
+            } else {
+                idle = tc.y0 + 4 * warp >= ny;  // warp-uniform
             }
         }
         Packed k;
