@@ -94,3 +94,16 @@ def test_cube2048_through_slabs(afd, ctx):
     del d
     got = slabbed(afd, ctx, cube, K, 0.125, 30, "rational", 32, 8)
     assert torch.equal(got.view(torch.int32), ref.view(torch.int32))
+
+
+def test_slab_decomposition_gpu_step_single_rank(afd, ctx):
+    # slabs.filter_slab with the library's step on a CUDA slab, one rank (no
+    # neighbours: rounds of `halo` iterations, no exchange): the rounds equal
+    # one afd_filter call bit for bit
+    from paper_1609_03782_gb300 import slabs
+    cube = synth.cutout((20, 24, 32), 9)
+    own = torch.from_numpy(cube).cuda()
+    got = slabs.filter_slab(own, 0, 20, 20, 11, 4, slabs.gpu_step(ctx, 1.1, 0.1))
+    afd.afd_sync(ctx)
+    ref = whole(afd, ctx, cube, 1.1, 0.1, 11, "rational")
+    assert torch.equal(got.cpu().view(torch.int32), ref.view(torch.int32))
