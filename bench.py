@@ -231,6 +231,30 @@ def pow2_near(v: float) -> float:
     return 2.0 ** math.floor(math.log2(v) + 0.5) if v > 0 and math.isfinite(v) else 1.0
 
 
+# Thread-instructions per voxel-iteration of the precision line's kernels
+# (ncu, full size; profiles/precision_instructions_cube512.md), keyed by
+# (storage, T); with the issue rate of the GPU they give each row's issue
+# ceiling beside its HBM ceiling.
+INSTR_PER_VOXEL_ITER = {("f32", 1): 29.9,
+                        ("f16", 1): 30.86, ("f16", 2): 44.30, ("f16", 4): 41.14,
+                        ("bf16", 1): 30.86, ("bf16", 2): 44.30, ("bf16", 4): 41.14,
+                        ("i16", 1): 39.42, ("i16", 2): 47.89, ("i16", 4): 43.00}
+ISSUE_THREAD_INSTR_PER_S = 152 * 4 * 32 * 2.07e9   # SMs x schedulers x lanes x clock
+
+
+def ceilings(storage: str, T: int, value: float, peak_gbs: float):
+    """HBM and issue ceilings (Gvox-it/s) of a pass, the one that binds, and
+    the fraction of it reached."""
+    b = 4.0 if storage == "f32" else 2.0
+    hbm = peak_gbs / (2.0 * b / T)
+    ins = INSTR_PER_VOXEL_ITER.get((storage, T))
+    issue = ISSUE_THREAD_INSTR_PER_S / ins / 1e9 if ins else None
+    bound = "issue" if issue is not None and issue < hbm else "hbm"
+    lim = issue if bound == "issue" else hbm
+    return {"hbm_ceiling": hbm, "issue_ceiling": issue, "thread_instr_per_voxel_iter": ins,
+            "bound": bound, "frac_of_bound": value / lim}
+
+
 def line_precision(afd, ctx, cube, d_in, ref32, sig):
     """2-byte storage (per-cube power-of-two scale) x temporal depth on the
     benchmark cube; error against the float32 GPU result over the whole cube
@@ -258,9 +282,10 @@ def line_precision(afd, ctx, cube, d_in, ref32, sig):
             afd.afd_sync(ctx)
             got = back.cpu().numpy()
             err = np.abs(got - ref)
-            rows.append({"storage": st, "t_block": T, "ms": ms,
-                         "value": n_vox * N_ITER / (ms / 1e3) / 1e9,
+            value = n_vox * N_ITER / (ms / 1e3) / 1e9
+            rows.append({"storage": st, "t_block": T, "ms": ms, "value": value,
                          "bytes_per_voxel_iter": 4.0 / T,
+                         **ceilings(st, T, value, measured_peaks()[0]),
                          "err_vs_f32_max_sigma": float(err.max()) / sig,
                          "err_vs_f32_rms_sigma": float(np.sqrt(np.mean(err ** 2))) / sig,
                          "err_faint_max_sigma": float(err[faint].max()) / sig,
@@ -269,7 +294,10 @@ def line_precision(afd, ctx, cube, d_in, ref32, sig):
     return {"unit": UNIT, "scale": scale, "workload": "the headline cube, K = 1.0 sigma, "
             "dt = 1/8, 50 rational iterations, stored in 2 bytes with a power-of-two scale; "
             "t_block iterations per pass over HBM; errors against the float32 result over "
-            "the whole cube, in units of sigma (faint: |I| < 3 sigma)",
+            "the whole cube, in units of sigma (faint: |I| < 3 sigma); per row the HBM "
+            "ceiling (measured copy GB/s over 2 b / T bytes) and the issue ceiling (152 SMs x "
+            "4 x 32 lanes x 2.07 GHz over the ncu thread-instructions per voxel-iteration), "
+            "and which binds",
             "best": {"storage": best["storage"], "t_block": best["t_block"],
                      "value": best["value"]}, "rows": rows}
 
