@@ -74,6 +74,7 @@ def _run(world, shape, seed, n_iter, halo):
     (2, (12, 9, 10), 7, 3),    # rounds of 3, 3, 1
     (3, (17, 6, 8), 9, 4),     # uneven slabs (6, 6, 5), rounds of 4, 4, 1
     (2, (8, 5, 7), 4, 4),      # one round, halo = the slab
+    (4, (9, 5, 6), 5, 1),      # four ranks, one ghost plane per round, slabs of 3, 2, 2, 2
 ])
 def test_slab_ranks_equal_the_whole_cube(world, shape, n_iter, halo):
     got = _run(world, shape, 5, n_iter, halo)
