@@ -5,16 +5,18 @@
 //
 // Separable kernels (the box, and the Gaussian without rotation):
 // W = wx (x) wy (x) wz, and the in-cube weight factorises into per-axis sums,
-// so out = (wz * (wy * (wx * I))) / (Dx(x) Dy(y) Dz(z)) with zero outside the
-// cube, applied as two products with the rounded reciprocals of Dx Dy (per
+// so out = (wz * (wx * (wy * I))) / (Dx(x) Dy(y) Dz(z)) with zero outside the
+// cube (each output sums its taps y first, then x, then z, each in tap
+// order), applied as two products with the rounded reciprocals of Dx Dy (per
 // voxel column) and Dz (per plane).  One fused pass streams z: a CTA owns a
-// 64 x 16 column of the cube over a z-chunk; for every input plane it loads
-// the tile and its x/y halo into shared memory (zero outside), convolves
-// along x (a register sliding window per 4 outputs) into a second buffer,
-// then along y, and pushes the result into a register ring of the last
-// 2 RZ + 1 planes per voxel, from which each output plane takes its z sum.
-// HBM traffic: one read of the input (the halo rows come from L2) and one
-// write.
+// 64 x 16 column of the cube over a z-chunk; for every input plane it has
+// the tile and its x/y halo in shared memory (zero outside), takes the y
+// sums of the tile's rows over every column (two rows per loaded row), then
+// the x sums of each thread's 4 voxels (a register sliding window), and
+// keeps the last 2 RZ + 1 planes' sums per voxel (in registers for small
+// RZ, in shared memory from kSepSmemRingRz on), from which each output plane
+// takes its z sum.  HBM traffic: one read of the input (the halo rows come
+// from L2) and one write.
 //
 // Rotated Gaussians are not separable: their direct 3-D correlation is in
 // smooth_direct.cu.
