@@ -748,6 +748,7 @@ def run_afd(args):
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD,
                        "parallelism": "one independent cube per GPU" if world > 1 else "1 GPU",
+                       "input_sha256": synth.sha256(cube),
                        "l2": "inputs larger than L2 (268 MB cube in + 268 MB out + 268 MB "
                              "ping-pong scratch vs 129 MB L2); no flush",
                        "step": "afd_filter_rel: a1 noise rms, a2 K = 1.0 rms and coefficients "

@@ -259,3 +259,9 @@ def model_b(seed: int = 0):
     roi = (int(lo[0]), int(hi[0]), int(lo[1]), int(hi[1]), int(lo[2]), int(hi[2]))
     return cube, model, roi
 
+
+
+def sha256(cube: np.ndarray) -> str:
+    """SHA-256 of a cube's bytes (C order), to identify a generated input."""
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(cube).tobytes()).hexdigest()
