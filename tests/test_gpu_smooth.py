@@ -88,7 +88,13 @@ def test_gauss_axis_aligned_matches_oracle(afd, ctx, shape, fwhm):
 @pytest.mark.parametrize("fwhm,angles", [((3.0, 5.0, 2.0), (20.0, 30.0, 40.0)),
                                          ((4.0, 2.0, 2.0), (0.0, 0.0, 35.0)),
                                          ((2.0, 2.0, 3.0), (60.0, -10.0, 0.0)),
-                                         ((6.0, 6.0, 6.0), (10.0, 20.0, 30.0))])
+                                         ((6.0, 6.0, 6.0), (10.0, 20.0, 30.0)),
+                                         # x radius 1 (one 4-tap group), 12 and 13 (seven
+                                         # groups, the last partial), 7
+                                         ((0.7, 3.0, 2.0), (20.0, 0.0, 0.0)),
+                                         ((9.0, 1.5, 1.5), (0.0, 0.0, 6.0)),
+                                         ((9.5, 2.0, 1.2), (4.0, 3.0, 5.0)),
+                                         ((5.0, 1.0, 1.0), (0.0, 0.0, 3.0))])
 def test_gauss_rotated_matches_oracle(afd, ctx, shape, fwhm, angles):
     rng = np.random.default_rng(sum(shape) + int(sum(angles)))
     cube = rng.standard_normal(shape).astype(np.float32)
