@@ -58,8 +58,11 @@ SHAPES = [(1, 1, 1), (3, 2, 5), (7, 9, 13), (20, 17, 70), (33, 40, 129)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
+# (21, 3, 1): rx = 10, a 12-column x halo (two rounds of halo tasks for the
+# loader warp); (49, 1, 1): rx = 24, the largest; (1, 1, 25): rz = 12, the
+# largest z window (shared-memory ring)
 @pytest.mark.parametrize("N", [(1, 1, 1), (3, 3, 1), (5, 3, 3), (3, 5, 7), (9, 1, 1),
-                               (1, 1, 13)])
+                               (1, 1, 13), (21, 3, 1), (49, 1, 1), (1, 1, 25)])
 def test_box_matches_oracle(afd, ctx, shape, N):
     rng = np.random.default_rng(sum(shape) + sum(N))
     cube = (rng.standard_normal(shape) * 2.0 + 0.5).astype(np.float32)
