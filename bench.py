@@ -479,7 +479,7 @@ def line_slabs(afd, ctx, cube, sig):
         moved = rounds * (planes_in + nz) * plane
         rows.append({"slab_nz": slab_nz, "halo": halo, "rounds": rounds, "slabs": slabs,
                      "device_bytes": 4 * min(nz, slab_nz + 2 * halo) * plane,
-                     "s": sec, "value": n_vox * N_ITER / sec / 1e9,
+                     "s": sec, "samples_s": secs, "value": n_vox * N_ITER / sec / 1e9,
                      "host_link_GBs": moved / sec / 1e9})
     t0 = time.perf_counter()
     afd.afd_filter_host(ctx, h_in, h_out, K, DT, N_ITER, COND)
