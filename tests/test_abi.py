@@ -62,6 +62,27 @@ def test_host_side_rejections_need_no_gpu(libpath):
     assert lib.afd_destroy(None) == 0
     lib.afd_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     assert lib.afd_create(None, 0, None) == 1
+    vp, i64, f32, ci, f64 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_float, ctypes.c_int,
+                             ctypes.c_double)
+    # the other compute entry points reject a null context the same way
+    calls = {
+        "afd_filter_rel": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, ci, ci, vp],
+                           (None, None, None, 4, 4, 4, None, 1.0, 0.1, 1, 1, None)),
+        "afd_filter_host_async": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, ci, ci],
+                                  (None, None, None, 4, 4, 4, None, 1.0, 0.1, 1, 1)),
+        "afd_filter_slabs": ([vp, vp, vp, vp, i64, i64, i64, vp, f32, f32, ci, ci, i64, ci],
+                             (None, None, None, None, 4, 4, 4, None, 1.0, 0.1, 1, 1, 2, 1)),
+        "afd_smooth_box": ([vp, vp, vp, i64, i64, i64, vp], (None, None, None, 4, 4, 4, None)),
+        "afd_smooth_gauss": ([vp, vp, vp, i64, i64, i64, vp, vp, f32],
+                             (None, None, None, 4, 4, 4, None, None, 3.0)),
+        "afd_f_diagnostic": ([vp, vp, vp, vp, i64, i64, i64, vp, f64, f64, f64, f64, vp],
+                             (None, None, None, None, 4, 4, 4, None, 1.0, 1.0, 2.0, 1.0, None)),
+    }
+    for name, (argtypes, args) in calls.items():
+        fn = getattr(lib, name)
+        fn.argtypes = argtypes
+        fn.restype = ctypes.c_int
+        assert fn(*args) == 1, name
 
 
 def test_python_binding_has_every_entry_point():
