@@ -501,11 +501,12 @@ afd_status afd_serve_destroy(afd_serve *s);
  * device byte for itself, a real-time loop where an allocation (and the
  * device synchronisation it can cause) is not allowed, or a plug-in that is
  * given no allocator.  Such callers cannot create an afd_ctx, which owns
- * device memory, so this call takes no context.  It allocates nothing: the
- * ping-pong scratch and the error word are fixed-size arrays inside the
- * library's device image (AFD_NOALLOC_MAX_VOXELS floats, 32 MiB, plus 256
- * bytes), which a GPU holds from the first call on it until the process
- * exits.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ * device memory, so this call takes no context.  It allocates nothing: three
+ * fixed-size arrays inside the library's device image hold its state (the
+ * ping-pong scratch of AFD_NOALLOC_MAX_VOXELS floats, 32 MiB; a 256-byte
+ * error word; the streaming kernel's 8-byte tile counter), which a GPU holds
+ * from the first call on it until the process exits.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
  *
  *   in, out      DEVICE pointers to nx*ny*nz floats, caller-owned (in == out
  *                filters in place; other overlaps are rejected).
@@ -518,10 +519,11 @@ afd_status afd_serve_destroy(afd_serve *s);
  * Set-up: the first call on each device (with that device current) looks up
  * the arrays' device addresses; make that first call before any stream
  * capture.
- * Sharing: every call on a device uses the same arrays, which keep the last
- * call's contents (the call clears its error word itself).  Calls whose work
- * overlaps on the GPU (from several host threads or streams at once) race
- * on the scratch and corrupt each other's results: serialise them.
+ * Sharing: every call on a device uses the same three arrays, which keep
+ * the last call's contents (the call zeroes its error word and tile counter
+ * itself).  Calls whose work overlaps on the GPU (from several host threads
+ * or streams at once) race on all three (scratch, error word, tile counter)
+ * and corrupt each other's results: serialise them.
  * Synchronous: returns after the result is in `out`; AFD_ETIMEOUT if a
  * kernel's bounded wait expired, AFD_ECUDA on a CUDA error. */
 afd_status afd_filter_noalloc(const float *in, float *out, int64_t nx, int64_t ny, int64_t nz,

@@ -236,13 +236,8 @@ afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int
     if (st != AFD_OK)
         return st;
 
-    const bool inplace = (in == out);
-    auto dst_of = [&](int i) -> float * {
-        if (inplace)
-            return (i & 1) ? out : ctx->scratch;
-        return ((n_iter - 1 - i) & 1) ? ctx->scratch : out;
-    };
-    auto src_of = [&](int i) -> const float * { return i == 0 ? in : dst_of(i - 1); };
+    const afd::PassSeq q{kind, in, out, ctx->scratch, static_cast<int>(nx), static_cast<int>(ny),
+                         static_cast<int>(nz), k, n_iter, ctx->stream, &ctx->launches};
 
     const bool fits = stream_kernel_fits(in, out, nx) &&
                       (reinterpret_cast<uintptr_t>(ctx->scratch) & 15u) == 0;
@@ -276,45 +271,27 @@ afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int
             if (st != AFD_OK)
                 return st;
         }
-        const afd::StreamPlan plan =
+        afd::StreamPlan plan =
             afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny), static_cast<int>(nz),
                                 ctx->sm_count, ctx->stream_bps, ctx->zc_hint);
+        plan.kdev = kdev;
         e = tiles_reset(ctx);
         cudaEvent_t tend = nullptr;
         if (e == cudaSuccess && ctx->timing)
             e = timing_begin(ctx, &tend);
-        for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
-            const float *src = src_of(i);
-            const int m = (src == in) ? 0 : (src == out ? 1 : 2);
-            const afd_host::TraceRange pass_trace("pass");
-            afd::StreamPlan pl = plan;
-            pl.pdl = i > 0;
-            pl.kdev = kdev;
-            e = afd::launch_pm_stream(kind, maps[m], dst_of(i), static_cast<int>(nx),
-                                      static_cast<int>(ny), static_cast<int>(nz), k, pl,
-                                      ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream);
-            ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
-            ctx->launches++;
-        }
+        if (e == cudaSuccess)
+            e = afd::stream_passes(q, maps, plan, ctx->d_tiles, &ctx->tiles_base, ctx->d_err);
         if (e == cudaSuccess && tend) {
             e = cudaEventRecord(tend, ctx->stream);
             ctx->timed_passes += n_iter;
         }
     } else {
-        for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
-            e = afd::launch_pm_simple(kind, src_of(i), dst_of(i), static_cast<int>(nx),
-                                      static_cast<int>(ny), static_cast<int>(nz), k, ctx->stream);
-            ctx->launches++;
-        }
+        e = afd::simple_passes(q);
     }
+    if (e == cudaSuccess)
+        e = afd::passes_finish(q);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e);
-    if (dst_of(n_iter - 1) != out) {
-        e = cudaMemcpyAsync(out, dst_of(n_iter - 1), bytes, cudaMemcpyDeviceToDevice,
-                            ctx->stream);
-        if (e != cudaSuccess)
-            return cuda_fail(ctx, e);
-    }
     return AFD_OK;
 }
 

@@ -77,6 +77,36 @@ cudaError_t launch_pm_stream_s(int S, int cond, const CUtensorMap &tmap_in, void
                                cudaStream_t stream);
 void pm_stream_box(int S, int *box_w, int *box_h, int *hx);
 
+// ---- the float32 pass sequence (passes.cu) ---------------------------------
+// n_iter >= 1 passes in -> ... -> out.  Pass i reads pass_src(i) and writes
+// pass_dst(i).  Out of place (in != out) the destinations alternate between
+// out and scratch so that the last pass lands in out; in place they
+// alternate starting with scratch, and an odd count ends in scratch
+// (passes_finish then copies the result to out).
+struct PassSeq {
+    int kind;              // conductance kind (CondKind)
+    const float *in;
+    float *out;
+    float *scratch;        // a cube-sized buffer other than in and out
+    int nx, ny, nz;
+    Coef k;                // coefficients (ignored where plan.kdev is set)
+    int n_iter;
+    cudaStream_t stream;
+    uint64_t *launches;    // incremented per launch (may be null)
+};
+float *pass_dst(const float *in, float *out, float *scratch, int n_iter, int i);
+const float *pass_src(const float *in, float *out, float *scratch, int n_iter, int i);
+// Streaming passes; maps[0..2]: the TMA maps of in, out and scratch.  The
+// tile counter ctr must be zero before the first call of a sequence; *base is
+// advanced by plan.ntiles per launch.  Pass 0 is an ordinary launch, the
+// others are programmatic dependents of the pass before.
+cudaError_t stream_passes(const PassSeq &q, const CUtensorMap maps[3], const StreamPlan &plan,
+                          unsigned long long *ctr, unsigned long long *base, int *err);
+// One-voxel-per-thread passes (any nx, any alignment).
+cudaError_t simple_passes(const PassSeq &q);
+// Copy the last pass's result to out if it is not there already.
+cudaError_t passes_finish(const PassSeq &q);
+
 // ---- a resident batch of cubes (streaming kernel over many cubes) ---------
 // Per-cube descriptor in device memory.  Roles: 0 input (resident), 1 result,
 // 2 scratch.  Rows are padded to `px` elements (a multiple of 16 bytes), which

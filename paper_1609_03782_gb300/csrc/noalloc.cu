@@ -17,8 +17,9 @@
 // addresses, so the first call on each device, with that device current,
 // looks up their device addresses with cudaGetSymbolAddress and keeps them.
 //
-// The filter itself is the same as afd_filter_out's: the same kernels and the
-// same per-face arithmetic, so the results are bit-identical.
+// The filter itself is the same as afd_filter_out's: the same pass sequence
+// (passes.cu), kernels and per-face arithmetic, so the results are
+// bit-identical.
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -166,18 +167,12 @@ extern "C" afd_status afd_filter_noalloc(const float *in, float *out, int64_t nx
     if (e != cudaSuccess)
         return AFD_ECUDA;
 
-    // ---- passes: in -> ... -> out, alternating with the static scratch ----
-    const bool inplace = (in == out);
-    auto dst_of = [&](int i) -> float * {
-        if (inplace)
-            return (i & 1) ? out : s.scratch;
-        return ((n_iter - 1 - i) & 1) ? s.scratch : out;
-    };
-    auto src_of = [&](int i) -> const float * { return i == 0 ? in : dst_of(i - 1); };
-
+    // ---- passes: in -> ... -> out, alternating with the static scratch; the
+    // same pass sequence as the context entry points (passes.cu) ----
+    const int inx = static_cast<int>(nx), iny = static_cast<int>(ny), inz = static_cast<int>(nz);
+    const afd::PassSeq q{kind, in, out, s.scratch, inx, iny, inz, k, n_iter, stream, nullptr};
     const bool use_stream = (nx % 4) == 0 && (reinterpret_cast<uintptr_t>(in) & 15u) == 0 &&
                             (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
-    const int inx = static_cast<int>(nx), iny = static_cast<int>(ny), inz = static_cast<int>(nz);
     if (use_stream) {
         const float *bufs[3] = {in, out, s.scratch};
         CUtensorMap maps[3];
@@ -188,21 +183,13 @@ extern "C" afd_status afd_filter_noalloc(const float *in, float *out, int64_t nx
                                                          s.stream_bps, 0);
         e = cudaMemsetAsync(s.tiles, 0, sizeof(unsigned long long), stream);
         unsigned long long base = 0;
-        for (int i = 0; i < n_iter && e == cudaSuccess; ++i) {
-            const float *src = src_of(i);
-            const int m = (src == in) ? 0 : (src == out ? 1 : 2);
-            afd::StreamPlan pl = plan;
-            pl.pdl = i > 0;
-            e = afd::launch_pm_stream(kind, maps[m], dst_of(i), inx, iny, inz, k, pl, s.tiles,
-                                      base, s.err, stream);
-            base += static_cast<unsigned long long>(plan.ntiles);
-        }
+        if (e == cudaSuccess)
+            e = afd::stream_passes(q, maps, plan, s.tiles, &base, s.err);
     } else {
-        for (int i = 0; i < n_iter && e == cudaSuccess; ++i)
-            e = afd::launch_pm_simple(kind, src_of(i), dst_of(i), inx, iny, inz, k, stream);
+        e = afd::simple_passes(q);
     }
-    if (e == cudaSuccess && dst_of(n_iter - 1) != out)
-        e = cudaMemcpyAsync(out, dst_of(n_iter - 1), bytes, cudaMemcpyDeviceToDevice, stream);
+    if (e == cudaSuccess)
+        e = afd::passes_finish(q);
 
     // ---- synchronous: report a bounded-wait expiry of this call ----
     int code = 0;

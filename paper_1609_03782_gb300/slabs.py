@@ -38,19 +38,39 @@ def filter_slab(own: torch.Tensor, z0: int, z1: int, nz: int, n_iter: int, halo:
     """n_iter iterations of the whole cube, computed by the ranks of `group`
     (default: the world), each owning planes [z0, z1) of the cube in the
     same order as the ranks.  own: this rank's (z1 - z0, ny, nx) planes.
-    halo: iterations per round, at most z1 - z0 (a neighbour's ghost planes
-    are its edge planes).  Returns this rank's planes after n_iter iterations
-    (a new tensor, on own's device, in own's dtype).
+    halo: iterations per round, at most the smallest slab of the group (a
+    neighbour's ghost planes are its edge planes).  Returns this rank's
+    planes after n_iter iterations (a new tensor, on own's device, in own's
+    dtype).
 
     Every rank of the group must call this with the same nz, n_iter and halo.
+    Argument errors are raised on every rank alike, before any exchange.
     """
     S = z1 - z0
-    if own.dim() != 3 or own.shape[0] != S or not (0 <= z0 < z1 <= nz):
-        raise ValueError("own must hold planes [z0, z1) of the cube")
-    if halo < 1 or (n_iter > 0 and halo > S):
-        raise ValueError("halo must be >= 1 and at most the slab's planes")
+    # Every rank must reach the same verdict before any exchange: a rank that
+    # raised alone would leave its neighbours waiting in their sends and
+    # receives.  So each rank checks its own arguments, and one small MIN
+    # reduction over the group (this call's only collective, once per call,
+    # not on the data path) gives every rank the group's smallest slab and
+    # whether all ranks' own checks passed.
+    local_ok = own.dim() == 3 and own.shape[0] == S and 0 <= z0 < z1 <= nz
+    if dist.is_initialized() and dist.get_world_size(group) > 1:
+        v = torch.tensor([S if local_ok else 0, 1 if local_ok else 0, halo, -halo, n_iter,
+                          -n_iter], dtype=torch.int64, device=own.device)
+        dist.all_reduce(v, op=dist.ReduceOp.MIN, group=group)
+        min_slab, all_ok = int(v[0]), bool(v[1])
+        same = int(v[2]) == -int(v[3]) == halo and int(v[4]) == -int(v[5]) == n_iter
+    else:
+        min_slab, all_ok, same = S, local_ok, True
+    if not all_ok:
+        raise ValueError("own must hold planes [z0, z1) of the cube (on every rank)")
+    if not same:
+        raise ValueError("every rank must pass the same halo and n_iter")
     if n_iter < 0:
         raise ValueError("n_iter must be >= 0")
+    if halo < 1 or (n_iter > 0 and halo > min_slab):
+        raise ValueError("halo must be >= 1 and at most the smallest slab's planes (%d)"
+                         % min_slab)
     rank = dist.get_rank(group) if dist.is_initialized() else 0
     below, above = z0 > 0, z1 < nz       # neighbours: rank - 1 and rank + 1
     buf = own.new_zeros((S + 2 * halo,) + tuple(own.shape[1:]))

@@ -82,6 +82,43 @@ def test_slab_ranks_equal_the_whole_cube(world, shape, n_iter, halo):
     assert np.array_equal(got, ref)
 
 
+def _worker_bad_halo(rank, world, port, shape, halo, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        nz = shape[0]
+        z0, z1 = slabs.slab_bounds(nz, world, rank)
+        own = torch.zeros((z1 - z0,) + tuple(shape[1:]), dtype=torch.float64)
+        try:
+            slabs.filter_slab(own, z0, z1, nz, 6, halo, oracle_step)
+            out.put((rank, z1 - z0, "returned"))
+        except ValueError as e:
+            out.put((rank, z1 - z0, "ValueError: %s" % e))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_uneven_slabs_reject_a_halo_on_every_rank():
+    # nz = 9 over 2 ranks gives slabs of 5 and 4 planes.  halo = 5 fits the
+    # first rank's slab but not the second's: both ranks must raise (and
+    # neither may wait for the other in an exchange).
+    world, shape = 2, (9, 4, 6)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_bad_halo, args=(r, world, port, shape, 5, q))
+             for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=120) for _ in procs), key=lambda t: t[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [5, 4]
+    assert all(r[2].startswith("ValueError") and "smallest slab" in r[2] for r in res), res
+
+
 def test_too_few_ghosts_would_differ():
     # the check above has teeth: with halo planes but more iterations than
     # ghosts per round, the slab edges see the artificial faces
