@@ -43,10 +43,7 @@ WORKLOAD = ("cube512: 512x512x256 float32 (x, y, velocity), noise sigma=1, 4 dis
             "(i = 20/45/70/85 deg) + 1 faint tail, seed 0; rational g, K = 1.0 sigma "
             "(GPU FP64 noise rms), dt = 1/8, 50 iterations, zero-flux faces")
 FALLBACK_HBM_GBS = 6800.0
-PROFILE = os.path.join(ROOT, "profiles", "pm_step_stream_cube512.md")
-KERNEL_SOURCES = ["paper_1609_03782_gb300/csrc/pm_stream.cu",
-                  "paper_1609_03782_gb300/csrc/afd_math.cuh",
-                  "paper_1609_03782_gb300/csrc/afd_ptx.cuh"]
+FIGURES = os.path.join(ROOT, "profiles", "figures.json")
 
 
 def parse_args():
@@ -63,8 +60,20 @@ def parse_args():
                     help="extra lines measured after the headline (N=1 only): any of "
                          "paper, diagnostics, smoothing, precision, slabs, batch, serving, or "
                          "'none'")
-    ap.add_argument("--serve-seconds", type=float, default=4.0,
-                    help="arrival window per request rate of the serving line")
+    ap.add_argument("--serve-requests", type=int, default=10000,
+                    help="requests per arrival rate of the serving line (open loop)")
+    ap.add_argument("--serve-max-seconds", type=float, default=60.0,
+                    help="cap on the arrival window per rate of the serving line")
+    ap.add_argument("--saturation-requests", type=int, default=5000,
+                    help="requests of the serving line's closed-loop saturation run")
+    ap.add_argument("--no-cpu-openmp", action="store_true",
+                    help="skip the multithreaded CPU build's timing")
+    ap.add_argument("--split", choices=["cubes", "slabs"], default="cubes",
+                    help="with N ranks: 'cubes' gives every rank its own cube (weak "
+                         "scaling); 'slabs' splits ONE cube into z-slabs over the ranks, "
+                         "exchanging ghost planes each round (strong scaling)")
+    ap.add_argument("--slab-halo", type=int, default=10,
+                    help="ghost planes (= iterations per round) of --split slabs")
     return ap.parse_args()
 
 
@@ -79,26 +88,32 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+def files_hash(files) -> str:
+    """sha256 (first 16 hex digits) of the repository files, in order."""
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in files:
         with open(os.path.join(ROOT, rel), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+def figure(section: str, key: str):
+    """A figure of profiles/figures.json (taken from an ncu capture), or None
+    if it is absent or its sources have changed since the capture."""
     try:
-        text = open(PROFILE).read()
-    except OSError:
+        with open(FIGURES) as fh:
+            ent = json.load(fh)[section][key]
+        if files_hash(ent["files"]) != ent["sha256_16"]:
+            return None
+        return float(ent["value"])
+    except (OSError, KeyError, ValueError):
         return None
-    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
-    t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != kernel_source_hash():
-        return None
-    return float(t.group(1))
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the headline pass (ncu), if taken on the
+    current kernel source."""
+    return figure("dram_bytes_per_launch", "pm_step_stream_f32_cube512")
 
 
 class ClockSampler:
@@ -231,50 +246,115 @@ def pow2_near(v: float) -> float:
     return 2.0 ** math.floor(math.log2(v) + 0.5) if v > 0 and math.isfinite(v) else 1.0
 
 
-# Thread-instructions per voxel-iteration of the precision line's kernels
-# (ncu, full size; profiles/precision_instructions_cube512.md), keyed by
-# (storage, T); with the issue rate of the GPU they give each row's issue
-# ceiling beside its HBM ceiling.
-INSTR_PER_VOXEL_ITER = {("f32", 1): 29.9,
-                        ("f16", 1): 30.86, ("f16", 2): 44.30, ("f16", 4): 41.14,
-                        ("bf16", 1): 30.86, ("bf16", 2): 44.30, ("bf16", 4): 41.14,
-                        ("i16", 1): 39.42, ("i16", 2): 47.89, ("i16", 4): 43.00}
-ISSUE_THREAD_INSTR_PER_S = 152 * 4 * 32 * 2.07e9   # SMs x schedulers x lanes x clock
+class Issue:
+    """Thread-instruction issue rate of the GPU: SMs x 4 schedulers x 32
+    lanes x SM clock.  The SM count comes from the device, the clock from
+    the nvidia-smi samples of the headline's timed region (else the measured
+    peaks file's maximum)."""
+    sm_count = 152
+    sm_mhz = 2070.0
+
+    @classmethod
+    def rate(cls) -> float:
+        return cls.sm_count * 4 * 32 * cls.sm_mhz * 1e6
 
 
 def ceilings(storage: str, T: int, value: float, peak_gbs: float):
     """HBM and issue ceilings (Gvox-it/s) of a pass, the one that binds, and
-    the fraction of it reached."""
+    the fraction of it reached.  The issue ceiling needs the pass's
+    thread-instructions per voxel-iteration from an ncu capture of the
+    current source (profiles/figures.json)."""
     b = 4.0 if storage == "f32" else 2.0
     hbm = peak_gbs / (2.0 * b / T)
-    ins = INSTR_PER_VOXEL_ITER.get((storage, T))
-    issue = ISSUE_THREAD_INSTR_PER_S / ins / 1e9 if ins else None
+    ins = figure("thread_instr_per_voxel_iter", "%s/%d" % (storage, T))
+    issue = Issue.rate() / ins / 1e9 if ins else None
     bound = "issue" if issue is not None and issue < hbm else "hbm"
     lim = issue if bound == "issue" else hbm
     return {"hbm_ceiling": hbm, "issue_ceiling": issue, "thread_instr_per_voxel_iter": ins,
             "bound": bound, "frac_of_bound": value / lim}
 
 
+GATE_SIGMA = 1e-3   # the 2-byte error gate, in units of sigma
+
+
+def precision_boxes(cube):
+    """Four 16 x 32 x 32 boxes (z, y, x ranges) where the 2-byte results are
+    compared with the FP64 oracle: a corner (three cube faces), the box
+    around the brightest voxel (a disk centre), and two seeded random
+    positions (mostly noise and faint emission)."""
+    import numpy as np
+    nz, ny, nx = cube.shape
+    bz, by, bx = 16, 32, 32
+    zc, yc, xc = np.unravel_index(int(np.argmax(cube)), cube.shape)
+    clamp = lambda c, n, w: int(min(max(c - w // 2, 0), n - w))
+    boxes = [((0, bz), (0, by), (0, bx))]
+    z0, y0, x0 = clamp(zc, nz, bz), clamp(yc, ny, by), clamp(xc, nx, bx)
+    boxes.append(((z0, z0 + bz), (y0, y0 + by), (x0, x0 + bx)))
+    rng = np.random.default_rng(11)
+    for _ in range(2):
+        z0 = int(rng.integers(0, nz - bz + 1))
+        y0 = int(rng.integers(0, ny - by + 1))
+        x0 = int(rng.integers(0, nx - bx + 1))
+        boxes.append(((z0, z0 + bz), (y0, y0 + by), (x0, x0 + bx)))
+    return boxes
+
+
+def err_norms(got, ref, sig):
+    """max, rms, faint-band (|ref| < 3 sigma) max and rms of |got - ref|,
+    in units of sigma."""
+    import numpy as np
+    err = np.abs(got.astype(np.float64) - ref)
+    faint = np.abs(ref) < 3.0 * sig
+    return {"max": float(err.max()) / sig, "rms": float(np.sqrt(np.mean(err ** 2))) / sig,
+            "faint_max": float(err[faint].max()) / sig if faint.any() else 0.0,
+            "faint_rms": float(np.sqrt(np.mean(err[faint] ** 2))) / sig if faint.any() else 0.0}
+
+
 def line_precision(afd, ctx, cube, d_in, ref32, sig):
     """2-byte storage (per-cube power-of-two scale) x temporal depth on the
-    benchmark cube; error against the float32 GPU result over the whole cube
-    (the float32 path itself is within 1e-4 sigma of the FP64 oracle, which the
-    test-suite checks), in units of sigma."""
+    benchmark cube.  Errors are measured against the FP64 oracle on four
+    sampled boxes (computed through the domain of dependence: exact), and,
+    for context, against the float32 GPU result over the whole cube; in
+    units of sigma.  gate: RMS and faint-band max within 1e-3 sigma."""
     import numpy as np
     import torch
+    import oracle
     n_vox = cube.size
     K = K_SIGMA * sig
+    Kf = float(np.float32(K))
     scale = pow2_near(sig)
+    boxes = precision_boxes(cube)
+    t0 = time.perf_counter()
+    orc = [oracle.pm_filter_box(cube, bx, Kf, DT, N_ITER, COND) for bx in boxes]
+    oracle_s = time.perf_counter() - t0
+    sl = [tuple(slice(a, b) for a, b in bx) for bx in boxes]
+    orc_cat = np.concatenate([o.ravel() for o in orc])
+
+    def vs_oracle(full):
+        return err_norms(np.concatenate([full[q].ravel() for q in sl]), orc_cat, sig)
+
     dt = {"f16": torch.float16, "bf16": torch.bfloat16, "i16": torch.int16}
     ref = ref32.cpu().numpy()
     faint = np.abs(ref) < 3.0 * sig
-    rows = []
+    peak = measured_peaks()[0]
+    # float32 through the same entry point, timed on this run
+    o32 = torch.empty_like(d_in)
+    run32 = lambda: afd.afd_filter_ex(ctx, d_in, o32, "f32", 1.0, K, DT, N_ITER, COND, None, 1)
+    run32()
+    ms32 = _events_ms(run32, 5)
+    v32 = n_vox * N_ITER / (ms32 / 1e3) / 1e9
+    afd.afd_sync(ctx)
+    e32 = vs_oracle(o32.cpu().numpy())
+    rows = [{"storage": "f32", "t_block": 1, "ms": ms32, "value": v32, "speedup_vs_f32": 1.0,
+             "bytes_per_voxel_iter": 8.0, **ceilings("f32", 1, v32, peak),
+             "err_vs_oracle": e32,
+             "gate_pass": e32["rms"] <= GATE_SIGMA and e32["faint_max"] <= GATE_SIGMA}]
     for st in ("f16", "bf16", "i16"):
         q = torch.empty(cube.shape, dtype=dt[st], device=d_in.device)
         o = torch.empty_like(q)
         back = torch.empty_like(d_in)
         afd.afd_quantize(ctx, d_in, q, st, scale)
-        for T in (1, 2, 4):
+        for T in (1, 2, 4, 8):
             run = lambda: afd.afd_filter_ex(ctx, q, o, st, scale, K, DT, N_ITER, COND, None, T)
             run()
             ms = _events_ms(run, 5)
@@ -283,23 +363,31 @@ def line_precision(afd, ctx, cube, d_in, ref32, sig):
             got = back.cpu().numpy()
             err = np.abs(got - ref)
             value = n_vox * N_ITER / (ms / 1e3) / 1e9
+            eo = vs_oracle(got)
             rows.append({"storage": st, "t_block": T, "ms": ms, "value": value,
-                         "bytes_per_voxel_iter": 4.0 / T,
-                         **ceilings(st, T, value, measured_peaks()[0]),
-                         "err_vs_f32_max_sigma": float(err.max()) / sig,
-                         "err_vs_f32_rms_sigma": float(np.sqrt(np.mean(err ** 2))) / sig,
-                         "err_faint_max_sigma": float(err[faint].max()) / sig,
-                         "err_faint_rms_sigma": float(np.sqrt(np.mean(err[faint] ** 2))) / sig})
-    best = max(rows, key=lambda r: r["value"])
+                         "speedup_vs_f32": value / v32, "bytes_per_voxel_iter": 4.0 / T,
+                         **ceilings(st, T, value, peak),
+                         "err_vs_oracle": eo,
+                         "gate_pass": eo["rms"] <= GATE_SIGMA and eo["faint_max"] <= GATE_SIGMA,
+                         "err_vs_f32": {"max": float(err.max()) / sig,
+                                        "rms": float(np.sqrt(np.mean(err ** 2))) / sig,
+                                        "faint_max": float(err[faint].max()) / sig}})
+        del q, o, back
+    best = max(rows[1:], key=lambda r: r["value"])
     return {"unit": UNIT, "scale": scale, "workload": "the headline cube, K = 1.0 sigma, "
             "dt = 1/8, 50 rational iterations, stored in 2 bytes with a power-of-two scale; "
-            "t_block iterations per pass over HBM; errors against the float32 result over "
-            "the whole cube, in units of sigma (faint: |I| < 3 sigma); per row the HBM "
-            "ceiling (measured copy GB/s over 2 b / T bytes) and the issue ceiling (152 SMs x "
-            "4 x 32 lanes x 2.07 GHz over the ncu thread-instructions per voxel-iteration), "
-            "and which binds",
+            "t_block iterations per pass over HBM (afd_filter_ex); err_vs_oracle: against the "
+            "FP64 oracle on the float32 input over four 16x32x32 boxes %s (oracle through the "
+            "domain of dependence, exact; %.1f s of oracle), in units of sigma (faint: |I| < 3 "
+            "sigma); gate_pass: rms and faint max both <= 1e-3 sigma; err_vs_f32: against the "
+            "float32 GPU result over the whole cube; per row the HBM ceiling (measured copy "
+            "GB/s over 2 b / T bytes) and the issue ceiling (SMs x 4 x 32 lanes x sampled SM "
+            "clock over the ncu thread-instructions per voxel-iteration), and which binds"
+            % (boxes, oracle_s),
+            "issue_rate": {"sm_count": Issue.sm_count, "sm_mhz": Issue.sm_mhz},
             "best": {"storage": best["storage"], "t_block": best["t_block"],
-                     "value": best["value"]}, "rows": rows}
+                     "value": best["value"], "speedup_vs_f32": best["speedup_vs_f32"]},
+            "rows": rows}
 
 
 def line_paper_form(afd, ctx):
@@ -531,10 +619,15 @@ def line_batch(afd, ctx):
     return out
 
 
-def line_serving(afd, ctx, seconds):
-    """64 resident float16 cubes (21 x 128^3, 21 x 256^3, 22 x 512x512x128);
-    Poisson arrivals; each request a re-filter with K ~ U[0.5, 3] sigma and
-    1-50 iterations; admitted by free HBM; p50/p99 latency submit -> done."""
+def line_serving(afd, ctx, max_requests, max_seconds, saturation_requests):
+    """64 resident float16 cubes (21 x 128^3, 21 x 256^3, 22 x 512x512x128).
+    Open loop: Poisson arrivals at each rate, each request a re-filter with
+    K ~ U[0.5, 3] sigma and 1-50 iterations, admitted by free HBM; p50/p99
+    latency from the scheduled arrival to completion, until max_requests
+    have arrived or max_seconds have passed.  The slowest 1 % are split
+    into host lag, waiting for memory, waiting for a round and running.
+    Closed loop (saturation): as many requests outstanding as the service
+    has slots, a new one submitted as each completes."""
     import numpy as np
     import torch
     import synth
@@ -549,25 +642,33 @@ def line_serving(afd, ctx, seconds):
         afd.afd_batch_set(b, i, q)
         del t
     afd.afd_sync(ctx)
-    budget = 16 << 30
-    srv = afd.afd_serve_create(b, budget, 128)
+    budget, slots = 16 << 30, 128
+    srv = afd.afd_serve_create(b, budget, slots)
     rng = np.random.default_rng(0)
+    vox = [float(a) * bb * cc for a, bb, cc in shapes]
     res = {"unit": "ms", "workload": "64 resident float16 cubes (21 x 128^3, 21 x 256^3, "
-           "22 x 512x512x128, seed 0); Poisson arrivals for %.1f s per rate; each request a "
-           "random cube, K ~ U[0.5, 3] sigma_cube, n ~ U{1..50}, rational g, dt = 1/8; "
-           "HBM budget 16 GiB for results + scratch; latency from the scheduled arrival to "
-           "the completion of the request's last round" % seconds, "rates": []}
+           "22 x 512x512x128, seed 0); each request a random cube, K ~ U[0.5, 3] sigma_cube, "
+           "n ~ U{1..50}, rational g, dt = 1/8; HBM budget 16 GiB for results + scratch, %d "
+           "slots; open loop: Poisson arrivals until %d requests or %.0f s per rate, latency "
+           "from the scheduled arrival to the completion of the request's last round; "
+           "closed loop: %d requests with every slot kept busy" % (slots, max_requests,
+                                                                 max_seconds,
+                                                                 saturation_requests),
+           "rates": []}
+
+    def draw():
+        return (int(rng.integers(0, len(shapes))), float(rng.uniform(0.5, 3.0)),
+                int(rng.integers(1, 51)))
+
     for lam in (50, 100, 200, 500):
-        gaps = rng.exponential(1.0 / lam, size=int(lam * seconds * 3) + 10)
-        arrivals = np.cumsum(gaps)
-        arrivals = arrivals[arrivals < seconds]
-        reqs = [(int(rng.integers(0, len(shapes))), float(rng.uniform(0.5, 3.0)),
-                 int(rng.integers(1, 51))) for _ in arrivals]
-        lat, work, live, k = [], 0.0, {}, 0
+        n_req = int(min(max_requests, lam * max_seconds))
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
+        reqs = [draw() for _ in range(n_req)]
+        rec, work, live, k = [], 0.0, {}, 0
         t0 = time.perf_counter()
-        while k < len(arrivals) or live:
+        while k < n_req or live:
             now = time.perf_counter() - t0
-            while k < len(arrivals) and arrivals[k] <= now:
+            while k < n_req and arrivals[k] <= now:
                 c, ks, n = reqs[k]
                 lag = (time.perf_counter() - t0) - arrivals[k]
                 tk = afd.afd_serve_submit(srv, c, ks * sig[c], DT, n, COND)
@@ -578,24 +679,197 @@ def line_serving(afd, ctx, seconds):
                 st, l = afd.afd_serve_poll(srv, tk)
                 if st == 2:
                     lag, c, n = live.pop(tk)
-                    lat.append((l + lag) * 1e3)
-                    a, bb, cc = shapes[c]
-                    work += float(a) * bb * cc * n
+                    ts = afd.afd_serve_times(srv, tk)
+                    rec.append((l + lag, lag, ts[1] - ts[0], ts[2] - ts[1], ts[3] - ts[2], c, n))
+                    work += vox[c] * n
                     afd.afd_serve_release(srv, tk)
-            if not live and k < len(arrivals):
+            if not live and k < n_req:
                 time.sleep(max(0.0, min(0.001, arrivals[k] - (time.perf_counter() - t0))))
         el = time.perf_counter() - t0
-        lat = np.array(lat)
-        res["rates"].append({"lambda_per_s": lam, "requests": int(len(lat)),
-                             "p50_ms": float(np.percentile(lat, 50)),
-                             "p99_ms": float(np.percentile(lat, 99)),
-                             "mean_ms": float(lat.mean()),
-                             "throughput_req_per_s": len(lat) / el,
-                             "throughput_gvox_iter_per_s": work / el / 1e9})
+        lat = np.array([r[0] for r in rec]) * 1e3
+        p99 = float(np.percentile(lat, 99))
+        tail = [r for r in rec if r[0] * 1e3 >= p99]
+        med = lambda j: float(np.median([r[j] for r in tail])) * 1e3
+        res["rates"].append({
+            "lambda_per_s": lam, "requests": int(len(lat)), "seconds": el,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": p99,
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "throughput_req_per_s": len(lat) / el,
+            "throughput_gvox_iter_per_s": work / el / 1e9,
+            "slowest_1pct": {"count": len(tail), "median_host_lag_ms": med(1),
+                             "median_wait_memory_ms": med(2), "median_wait_round_ms": med(3),
+                             "median_run_ms": med(4),
+                             "median_iterations": float(np.median([r[6] for r in tail])),
+                             "share_512x512x128": sum(1 for r in tail if vox[r[5]] > 2 ** 25)
+                             / max(1, len(tail))}})
+    # closed loop: keep every slot busy
+    live, done, work = set(), 0, 0.0
+    n_sub = 0
+    t0 = time.perf_counter()
+    while done < saturation_requests:
+        while len(live) < slots and n_sub < saturation_requests:
+            c, ks, n = draw()
+            live.add((afd.afd_serve_submit(srv, c, ks * sig[c], DT, n, COND), c, n))
+            n_sub += 1
+        afd.afd_serve_step(srv, wait=True)
+        for item in list(live):
+            if afd.afd_serve_poll(srv, item[0])[0] == 2:
+                live.discard(item)
+                afd.afd_serve_release(srv, item[0])
+                done += 1
+                work += vox[item[1]] * item[2]
+    el = time.perf_counter() - t0
+    res["saturation"] = {"requests": done, "seconds": el, "req_per_s": done / el,
+                         "saturation_gvox_iter_per_s": work / el / 1e9}
     srv.close()
     b.close()
     torch.cuda.synchronize()
     return res
+
+
+def cpu_openmp_baseline(cube, K):
+    """The multithreaded FP32 CPU build (cpu_omp, OpenMP) on the full
+    benchmark cube on every host core the process may use: median of 5 runs
+    after 1 warm-up; host STREAM-copy bandwidth as its roofline."""
+    import numpy as np
+    import cpu_omp
+    cpu_omp.build()
+    cores = cpu_cores()
+    work = np.empty_like(cube)
+    secs = []
+    for r in range(6):
+        np.copyto(work, cube)
+        t0 = time.perf_counter()
+        cpu_omp.filter_inplace(work, K, DT, N_ITER, COND, threads=cores)
+        el = time.perf_counter() - t0
+        if r > 0:
+            secs.append(el)
+    sec = statistics.median(secs)
+    value = cube.size * N_ITER / sec / 1e9
+    host_gbs = cpu_omp.stream_copy_gbs(1 << 30, 5, cores)
+    achieved = 8.0 * cube.size * N_ITER / sec / 1e9
+    return {"value": value, "unit": UNIT, "cores": cores, "threads": cores,
+            "kind": "openmp_f32", "cpu_model": cpu_omp.cpu_model(),
+            "sample": "the full 512x512x256 cube, 50 rational iterations, float32, per-face "
+                      "conductance, OpenMP over z slabs (cpu_omp/afd_omp.c, gcc -O3 -fopenmp, "
+                      "no target-specific flags); median of 5 runs after 1 warm-up",
+            "s_per_run": sec, "samples_s": secs,
+            "roofline": {"bound": "host memory", "achieved": achieved, "peak": host_gbs,
+                         "unit": "GB/s", "frac": achieved / host_gbs if host_gbs > 0 else None,
+                         "peak_kind": "measured STREAM copy (read + write) on the same host "
+                                      "cores, 1 GiB per buffer, best of 5",
+                         "bytes_per_voxel_iter": 8.0}}
+
+
+def summary(line):
+    """The line's key figures in a few hundred characters (rounded)."""
+    r3 = lambda v: None if v is None else float("%.3g" % v)
+    out = {"value": r3(line["value"]), "roofline_frac": r3(line["roofline"]["frac"]),
+           "e2e": r3(line["e2e"]["value"])}
+    if line.get("cpu_openmp"):
+        c = line["cpu_openmp"]
+        out["cpu_openmp"] = {"value": r3(c["value"]), "cores": c["cores"],
+                             "host_frac": r3(c["roofline"]["frac"])}
+    if line.get("cpu_baseline"):
+        out["cpu_oracle"] = r3(line["cpu_baseline"]["value"])
+    L = line.get("lines", {})
+    if "precision" in L:
+        out["precision"] = [[r["storage"], r["t_block"], r3(r["value"]),
+                             r3(r["speedup_vs_f32"]), r3(r["err_vs_oracle"]["rms"]),
+                             r3(r["err_vs_oracle"]["faint_max"]), r["gate_pass"]]
+                            for r in L["precision"]["rows"]]
+        out["precision_cols"] = "storage,T,Gvox-it/s,x f32,rms/sig,faint max/sig,gate"
+    if "batch" in L:
+        out["batch"] = {k: r3(L["batch"][k]["value"]) for k in ("f32", "f16") if k in L["batch"]}
+    if "serving" in L:
+        sv = L["serving"]
+        out["serving"] = [[r["lambda_per_s"], r["requests"], r3(r["p50_ms"]), r3(r["p99_ms"])]
+                          for r in sv["rates"]]
+        out["serving_cols"] = "lambda,requests,p50 ms,p99 ms"
+        if "saturation" in sv:
+            out["saturation_gvox_iter_per_s"] = r3(sv["saturation"]["saturation_gvox_iter_per_s"])
+    return out
+
+
+def split_slabs_run(cube, world, rank, n_iter, halo, step, steps, to_device, sync):
+    """One cube over `world` ranks (rank `rank` here): this rank's z-slab of
+    the numpy cube, moved by to_device, filtered `steps` times by
+    slabs.filter_slab (ghost-plane exchange with the neighbour ranks each
+    round of `halo` iterations, `step` doing the arithmetic); sync() before
+    and after the timed loop.  Returns (z0, z1, the slab's last result,
+    seconds for the `steps` calls)."""
+    from paper_1609_03782_gb300 import slabs
+    nz = cube.shape[0]
+    z0, z1 = slabs.slab_bounds(nz, world, rank)
+    own = to_device(cube[z0:z1])
+    res = None
+    sync()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        res = slabs.filter_slab(own, z0, z1, nz, n_iter, halo, step)
+    sync()
+    return z0, z1, res, time.perf_counter() - t0
+
+
+def run_slabs(args):
+    """--split slabs: the headline cube split into z-slabs over the ranks
+    (strong scaling): every round of `halo` iterations each rank swaps `halo`
+    edge planes with its neighbours (NCCL point-to-point into its own
+    buffer, no remote loads) and filters its slab with its ghost planes."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import synth
+    from paper_1609_03782_gb300 import afd, ranks, slabs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    cube = synth.cube512()
+    ctx = afd.afd_create(local)
+    whole = torch.from_numpy(cube).to(dev)
+    sig = afd.afd_noise_rms(ctx, whole)
+    K = K_SIGMA * sig
+    step = slabs.gpu_step(ctx, K, DT, COND)
+    to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    def sync():
+        torch.cuda.synchronize(dev)
+        ranks.barrier()
+
+    split_slabs_run(cube, world, rank, N_ITER, args.slab_halo, step, max(args.warmup, 1),
+                    to_dev, sync)
+    z0, z1, res, sec = split_slabs_run(cube, world, rank, N_ITER, args.slab_halo, step,
+                                       args.steps, to_dev, sync)
+    sec = ranks.max_over_ranks(sec, dev)
+    # the slab result against the library's whole-cube filter, bit for bit
+    ref = torch.empty_like(whole)
+    afd.afd_filter_out(ctx, whole, ref, K, DT, N_ITER, COND)
+    afd.afd_sync(ctx)
+    mism = float(0.0 if torch.equal(res, ref[z0:z1]) else 1.0)
+    mism = ranks.max_over_ranks(mism, dev)
+    value = cube.size * N_ITER * args.steps / sec / 1e9
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": sec / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD + " (K fixed before the timed region)",
+                           "parallelism": "z-slabs over %d ranks, %d ghost planes per round"
+                                          % (world, args.slab_halo),
+                           "step": "slabs.filter_slab: per round of %d iterations a ghost-"
+                                   "plane exchange (NCCL send/recv into each rank's own "
+                                   "buffer) and afd_filter on the slab" % args.slab_halo},
+                "bit_exact_vs_whole_cube": mism == 0.0}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
 
 
 # ----------------------------------------------------------------------------
@@ -668,6 +942,15 @@ def run_afd(args):
     afd.afd_sync(ctx)
     launches = afd.afd_launch_count(ctx) - launches0
     ms = max_over_ranks(t0.elapsed_time(t1))
+    Issue.sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    if clk and clk.get("sm_mhz"):
+        Issue.sm_mhz = float(clk["sm_mhz"])
+    else:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                Issue.sm_mhz = float(json.load(fh)["sm_max_mhz"])
+        except (OSError, KeyError, ValueError):
+            pass
     afd.afd_pass_timing(ctx, False)
     filt_ms, filt_passes = afd.afd_pass_timing_read(ctx)
     assert filt_passes == args.steps * N_ITER, filt_passes
@@ -729,10 +1012,14 @@ def run_afd(args):
         if "batch" in want:
             lines["batch"] = line_batch(afd, ctx)
         if "serving" in want:
-            lines["serving"] = line_serving(afd, ctx, args.serve_seconds)
+            lines["serving"] = line_serving(afd, ctx, args.serve_requests,
+                                            args.serve_max_seconds, args.saturation_requests)
 
     line = None
     if rank == 0:
+        cpu_mt = None
+        if world == 1 and not args.no_cpu_openmp:
+            cpu_mt = cpu_openmp_baseline(cube, K_SIGMA * sig)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             shape = (128, 256, 256)
@@ -763,6 +1050,7 @@ def run_afd(args):
                          "bytes_per_launch": bytes_per_launch,
                          "launch_ms": launch_ms, "traffic": profiled_traffic()},
             "cpu_baseline": cpu,
+            "cpu_openmp": cpu_mt,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * n_vox,
                     "d2h_bytes_per_step": 4 * n_vox,
                     "path": "afd_filter_host_async, one call per step (a stream of cubes): "
@@ -779,6 +1067,8 @@ def run_afd(args):
             "sum_drift_rel": drift,
             "lines": lines,
         }
+        # last, so that a reader that keeps only the end of the line keeps it
+        line["summary"] = summary(line)
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -790,6 +1080,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.split == "slabs":
+        return run_slabs(args)
     return run_afd(args)
 
 

@@ -480,6 +480,14 @@ afd_status afd_serve_poll(afd_serve *s, uint64_t ticket, int *state, double *lat
  * if not done. */
 afd_status afd_serve_result(afd_serve *s, uint64_t ticket, void *dst);
 
+/* Host timestamps of a request (seconds on the library's steady clock):
+ * out4[0] submitted, out4[1] admitted (slot memory granted; -1 while
+ * queued), out4[2] its first iteration's round launched (-1 before),
+ * out4[3] its last round seen complete (-1 before).  They split a latency
+ * into waiting for memory, waiting for a round and running.  AFD_EINVAL for
+ * an unknown (or released) ticket. */
+afd_status afd_serve_times(afd_serve *s, uint64_t ticket, double *out4);
+
 /* Free a done request's slot memory (after its result has been copied).
  * AFD_EBUSY if not done. */
 afd_status afd_serve_release(afd_serve *s, uint64_t ticket);

@@ -84,6 +84,7 @@ def _load():
         "afd_serve_step": ([vp, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)], c_int),
         "afd_serve_poll": ([vp, ctypes.c_uint64, ctypes.POINTER(c_int),
                             ctypes.POINTER(ctypes.c_double)], c_int),
+        "afd_serve_times": ([vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)], c_int),
         "afd_serve_result": ([vp, ctypes.c_uint64, vp], c_int),
         "afd_serve_release": ([vp, ctypes.c_uint64], c_int),
         "afd_serve_free_bytes": ([vp, ctypes.POINTER(ctypes.c_size_t)], c_int),
@@ -608,6 +609,15 @@ def afd_serve_poll(srv: Server, ticket: int):
     _check(_lib.afd_serve_poll(srv.handle, int(ticket), ctypes.byref(st), ctypes.byref(lat)),
            "afd_serve_poll", srv.batch.ctx)
     return st.value, lat.value
+
+
+def afd_serve_times(srv: Server, ticket: int):
+    """(submitted, admitted, first round launched, done) host timestamps in
+    seconds (-1 for a stage not reached yet)."""
+    out = (ctypes.c_double * 4)()
+    _check(_lib.afd_serve_times(srv.handle, int(ticket), out), "afd_serve_times",
+           srv.batch.ctx)
+    return tuple(out)
 
 
 def afd_serve_result(srv: Server, ticket: int, out: torch.Tensor) -> torch.Tensor:

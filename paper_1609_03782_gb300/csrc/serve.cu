@@ -51,7 +51,7 @@ struct Req {
     int finished = 0;  // iterations whose round has completed
     int slot = -1;
     size_t off = 0, bytes = 0;  // slot memory: result at off, scratch at off + bytes/2
-    double t_submit = 0.0, t_done = 0.0;
+    double t_submit = 0.0, t_admit = 0.0, t_launch = 0.0, t_done = 0.0;
     int state = REQ_QUEUED;
 };
 
@@ -224,6 +224,7 @@ afd_status admit(afd_serve *s)
         if (e != cudaSuccess)
             return cuda_fail(s->ctx, e);
         q.state = REQ_ACTIVE;
+        q.t_admit = now_s();
         s->queue.pop_front();
     }
     return AFD_OK;
@@ -244,6 +245,8 @@ afd_status launch_round(afd_serve *s, bool *launched)
         if (q.state != REQ_ACTIVE || q.issued >= q.n_iter)
             continue;
         const int i = q.issued;
+        if (i == 0)
+            q.t_launch = now_s();
         const int dst = ((q.n_iter - 1 - i) & 1) ? 2 : 1;
         const int src = i == 0 ? 0 : (((q.n_iter - i) & 1) ? 2 : 1);
         roles[q.slot] = make_int2(src, dst);
@@ -431,6 +434,21 @@ afd_status afd_serve_poll(afd_serve *s, uint64_t ticket, int *state, double *lat
     *state = it->second.state;
     if (latency_s)
         *latency_s = it->second.state == REQ_DONE ? it->second.t_done - it->second.t_submit : -1.0;
+    return AFD_OK;
+}
+
+afd_status afd_serve_times(afd_serve *s, uint64_t ticket, double *out4)
+{
+    if (!s || !out4)
+        return AFD_EINVAL;
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end())
+        return AFD_EINVAL;
+    const Req &q = it->second;
+    out4[0] = q.t_submit;
+    out4[1] = q.state >= REQ_ACTIVE ? q.t_admit : -1.0;
+    out4[2] = q.issued > 0 ? q.t_launch : -1.0;
+    out4[3] = q.state == REQ_DONE ? q.t_done : -1.0;
     return AFD_OK;
 }
 

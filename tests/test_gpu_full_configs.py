@@ -4,17 +4,21 @@
   seed 0), K_i = 1.5 sigma_i from the GPU noise estimate, 20 rational
   iterations, float32 and float16-stored, in one graph launch: every cube is
   bit-identical to the same filter on that cube alone (compared on the
-  device), its K matches the FP64 noise estimate, and ten cubes are checked
-  against the FP64 oracle.
+  device), its K matches the FP64 noise estimate, and ten float32 cubes and
+  three float16 cubes are checked against the FP64 oracle (the float16 ones
+  within the storage-rounding bound of test_gpu_precision.py).
 * 64 resident float16 cubes (21 x 128^3, 21 x 256^3, 22 x 512x512x128): a mix
   of re-filter requests, some submitted while others run, each bit-identical
-  to the same request run alone.
+  to the same request run alone; three served results (one per cube class)
+  are checked against the FP64 oracle within the same bound, the
+  512 x 512 x 128 one on sampled boxes through the domain of dependence.
 """
 import numpy as np
 import pytest
 
 import oracle
 import synth
+from test_gpu_precision import rounding_bounds
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -73,6 +77,24 @@ def test_300_cutouts(afd, ctx, storage):
                 got = afd.afd_batch_get(b, int(i), torch.empty(shapes[i], device="cuda"))
                 o = oracle.pm_filter(cubes[i], float(Kused[i]), DT, 20, "rational")
                 assert np.abs(got.cpu().numpy() - o).max() <= 1e-4, int(i)
+        else:
+            # three float16 cubes (smallest, median, largest) against the FP64
+            # oracle on the float32 input, within the storage-rounding bound
+            order = np.argsort([a * bb * cc for a, bb, cc in shapes])
+            for i in (order[0], order[150], order[-1]):
+                i = int(i)
+                got = afd.afd_batch_get(b, i, torch.empty(shapes[i], dtype=tdt, device="cuda"))
+                back = torch.empty(shapes[i], dtype=torch.float32, device="cuda")
+                afd.afd_dequantize(ctx, got, back, "f16", 1.0)
+                afd.afd_sync(ctx)
+                o = oracle.pm_filter(cubes[i], float(Kused[i]), DT, 20, "rational")
+                err = np.abs(back.cpu().numpy() - o)
+                bmax, bfaint = rounding_bounds("f16", "rational", DT, 20, 1,
+                                               float(np.abs(cubes[i]).max()), 1.0)
+                assert err.max() <= bmax, (i, float(err.max()), bmax)
+                faint = np.abs(o) < 3.0
+                frms = float(np.sqrt(np.mean(err[faint] ** 2)))
+                assert frms <= bfaint, (i, frms, bfaint)
     finally:
         b.close()
 
@@ -105,7 +127,13 @@ def test_serving_64_resident(afd, ctx):
             afd.afd_serve_step(srv, wait=True)
             if all(afd.afd_serve_poll(srv, t)[0] == 2 for t in tickets):
                 break
-        for t, (c, ks, n) in zip(tickets, reqs):
+        # one served request per cube class is also checked against the FP64
+        # oracle on the float32 cube
+        checked = {}
+        for k, (c, ks, n) in enumerate(reqs):
+            checked.setdefault(tuple(shapes[c]), k)
+        assert len(checked) == 3, checked
+        for k, (t, (c, ks, n)) in enumerate(zip(tickets, reqs)):
             assert afd.afd_serve_poll(srv, t)[0] == 2
             got = afd.afd_serve_result(srv, t, torch.empty_like(qs[c]))
             ref = torch.empty_like(qs[c])
@@ -113,8 +141,40 @@ def test_serving_64_resident(afd, ctx):
                               None, 1)
             afd.afd_sync(ctx)
             assert torch.equal(got.view(torch.int16), ref.view(torch.int16)), (t, c, n)
+            if k in checked.values():
+                served_vs_oracle(afd, ctx, got, c, float(np.float32(ks * sig[c])), n)
             afd.afd_serve_release(srv, t)
     finally:
         if srv is not None:
             srv.close()
         b.close()
+
+
+def served_vs_oracle(afd, ctx, got, c, K, n):
+    """A served float16 result against the FP64 oracle on the float32 cube,
+    within the storage-rounding bound (max norm and faint-band rms).  Cubes
+    up to 256^3 are compared whole; a 512 x 512 x 128 cube on three sampled
+    boxes (a corner, an inner box and a box across the far faces), each
+    computed by the oracle from the box grown by n voxels (exact)."""
+    cube = synth.serving_cube(c)
+    back = torch.empty(cube.shape, dtype=torch.float32, device="cuda")
+    afd.afd_dequantize(ctx, got, back, "f16", 1.0)
+    afd.afd_sync(ctx)
+    g = back.cpu().numpy()
+    nz, ny, nx = cube.shape
+    if cube.size <= 256 ** 3:
+        boxes = [((0, nz), (0, ny), (0, nx))]
+    else:
+        boxes = [((0, 24), (0, 40), (0, 40)),
+                 ((nz // 2 - 12, nz // 2 + 12), (ny // 2 - 20, ny // 2 + 20),
+                  (nx // 2 - 20, nx // 2 + 20)),
+                 ((nz - 24, nz), (ny - 40, ny), (nx - 40, nx))]
+    bmax, bfaint = rounding_bounds("f16", "rational", DT, n, 1, float(np.abs(cube).max()), 1.0)
+    for box in boxes:
+        o = oracle.pm_filter_box(cube, box, K, DT, n, "rational")
+        sl = tuple(slice(a, b) for a, b in box)
+        err = np.abs(g[sl] - o)
+        assert err.max() <= bmax, (c, box, float(err.max()), bmax)
+        faint = np.abs(o) < 3.0
+        frms = float(np.sqrt(np.mean(err[faint] ** 2)))
+        assert frms <= bfaint, (c, box, frms, bfaint)
