@@ -585,8 +585,8 @@ def line_slabs(afd, ctx, cube, sig):
 
 def line_batch(afd, ctx):
     """300 galaxy cutouts of uneven size, K_i = 1.5 sigma_i (GPU FP64 noise
-    estimate), 20 iterations, one CUDA-graph launch per call; z-chunk picked
-    by the autotuner."""
+    estimate), 20 iterations, one CUDA-graph launch per call; tile kind and
+    z-chunk picked by the autotuner."""
     import torch
     import synth
     from paper_1609_03782_gb300 import tune
@@ -608,11 +608,12 @@ def line_batch(afd, ctx):
                 t = q
             afd.afd_batch_set(b, i, t)
         K = [-1.5] * len(shapes)
-        zc = tuner.tune_batch(afd, b, K, DT, 20, COND)
+        tiles, zc = tuner.tune_batch(afd, b, K, DT, 20, COND)
         run = lambda: afd.afd_batch_filter(b, K, DT, 20, COND)
         run()
         ms = _events_ms(run, 10)
-        out[st] = {"ms_per_call": ms, "value": nvox * 20 / (ms / 1e3) / 1e9, "zchunk": zc,
+        out[st] = {"ms_per_call": ms, "value": nvox * 20 / (ms / 1e3) / 1e9, "tiles": tiles,
+                   "zchunk": zc,
                    "tuning_ms": tuner.cache[tune.batch_key(shapes, st, COND, 20)]["ms"]}
         b.close()
         torch.cuda.synchronize()

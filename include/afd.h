@@ -99,7 +99,9 @@ afd_status afd_set_stream(afd_ctx *ctx, void *cuda_stream);
 
 /* Choose the kernel family used by afd_filter (default AFD_KERNEL_AUTO).
  * AFD_KERNEL_STREAM on a cube it cannot handle makes afd_filter return
- * AFD_EINVAL.  All kernels give bit-identical results. */
+ * AFD_EINVAL.  For afd_filter_ex's depth-1 passes on 2-byte storage, AUTO
+ * runs the 8 x 2-voxel-per-thread streaming kernel and STREAM the 4 x 2 one.
+ * All kernels give bit-identical results. */
 afd_status afd_set_kernel(afd_ctx *ctx, afd_kernel kernel);
 
 /* Tuning knob of the streaming kernel: the largest number of z planes one
@@ -434,6 +436,19 @@ afd_status afd_batch_k(afd_batch *b, float *K_out);
 /* Tuning: z planes per tile of the batched streaming kernel (0 = 64).
  * Results do not depend on it. */
 afd_status afd_batch_set_zchunk(afd_batch *b, int zc);
+
+/* Tile kinds of the batched pass (afd_batch_set_tiles). */
+#define AFD_TILES_64X32 0 /* 64 x 32 tiles, 4 x 2 voxels per thread            */
+#define AFD_TILES_WIDE 1  /* per-cube tiles of 8 x 2 voxels per thread: tile
+                             columns of at most 128 voxels and equal width,
+                             as tall as the CTA's threads cover (narrow cubes
+                             get one tall tile column, no halo columns
+                             between tiles); the default                   */
+
+/* Tuning: the tile kind of the batch's passes (and of a service over it).
+ * Results do not depend on it (every kind computes the same per-face
+ * arithmetic, bit for bit).  AFD_EINVAL for another value. */
+afd_status afd_batch_set_tiles(afd_batch *b, int kind);
 
 /* Free the batch's device memory after the context's stream is idle.  NULL
  * is accepted. */

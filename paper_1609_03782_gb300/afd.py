@@ -77,6 +77,7 @@ def _load():
         "afd_batch_filter": ([vp, vp, vp, f32, c_int, c_int], c_int),
         "afd_batch_k": ([vp, vp], c_int),
         "afd_batch_set_zchunk": ([vp, c_int], c_int),
+        "afd_batch_set_tiles": ([vp, c_int], c_int),
         "afd_batch_destroy": ([vp], c_int),
         "afd_serve_create": ([vp, vp, ctypes.c_size_t, c_int, ctypes.POINTER(vp)], c_int),
         "afd_serve_submit": ([vp, c_int, f32, f32, c_int, c_int,
@@ -552,6 +553,16 @@ def afd_batch_k(b: Batch):
 def afd_batch_set_zchunk(b: Batch, zc: int) -> None:
     _use_current_stream(b.ctx)
     _check(_lib.afd_batch_set_zchunk(b.handle, int(zc)), "afd_batch_set_zchunk", b.ctx)
+
+
+TILES = {"64x32": 0, "wide": 1}
+
+
+def afd_batch_set_tiles(b: Batch, kind: str) -> None:
+    """Tile kind of the batch's passes: '64x32' (4 x 2 voxels per thread) or
+    'wide' (per-cube tiles of 8 x 2 voxels per thread, the default)."""
+    _use_current_stream(b.ctx)
+    _check(_lib.afd_batch_set_tiles(b.handle, TILES[kind]), "afd_batch_set_tiles", b.ctx)
 
 
 def afd_batch_destroy(b: Batch) -> None:

@@ -1260,7 +1260,43 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
     for (int i = 0; i < npass; ++i) {
         const afd_host::TraceRange pass_trace("pass");
         const int T = depth_of(i);
-        if (fits && T == 1) {
+        if (fits && T == 1 && S != afd::STORE_F32 && ctx->kernel != AFD_KERNEL_STREAM) {
+            // depth 1 on 2-byte storage: the 8 x 2-voxel streaming kernel
+            if (ctx->wide_bps == 0) {
+                e = afd::pm_wide_prepare();
+                if (e == cudaSuccess)
+                    e = afd::pm_wide_occupancy(&ctx->wide_bps);
+                if (e != cudaSuccess)
+                    return cuda_fail(ctx, e);
+                if (ctx->wide_bps < 1)
+                    ctx->wide_bps = 1;
+            }
+            int bw = 0, bh = 0;
+            afd::pm_wide_box(S, &bw, &bh);
+            CUtensorMap map;
+            st = encode_box_map(ctx, &map, src_of(i), S, bw, bh, static_cast<int>(nx),
+                                static_cast<int>(ny), static_cast<int>(nz));
+            if (st != AFD_OK)
+                return st;
+            afd::StreamPlan plan =
+                afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
+                                    static_cast<int>(nz), ctx->sm_count, ctx->wide_bps,
+                                    ctx->zc_hint, afd::kWideTX, afd::kWideTY);
+            plan.pdl = prev_stream;
+            prev_stream = true;
+            if (!tiles_zeroed) {
+                e = tiles_reset(ctx);
+                tiles_zeroed = true;
+            }
+            if (e == cudaSuccess)
+                e = afd::launch_pm_wide(S, kind, map, dst_of(i), static_cast<int>(nx),
+                                        static_cast<int>(ny), static_cast<int>(nz), k, plan,
+                                        ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream);
+            ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
+            ctx->launches++;
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e);
+        } else if (fits && T == 1) {
             // depth 1: the barrier-free streaming kernel, on the stored format
             if (ctx->stream_bps == 0) {
                 e = afd::pm_stream_prepare();

@@ -65,7 +65,20 @@ struct StreamPlan {
 size_t pm_stream_smem_bytes();
 cudaError_t pm_stream_prepare();  // one-time kernel attributes
 cudaError_t pm_stream_occupancy(int *blocks_per_sm);
-StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_sm, int zc_hint);
+StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_sm, int zc_hint,
+                          int tile_x = kStreamTX, int tile_y = kStreamTY);
+
+// The planes [z0, z1) of z-chunk tz of a plan's ZLevels.
+__host__ __device__ inline void zchunk(const ZLevels &lv, int tz, int &z0, int &z1)
+{
+    if (tz < lv.nuni) {
+        z0 = tz * lv.zlen + (tz < lv.zrem ? tz : lv.zrem);
+        z1 = z0 + lv.zlen + (tz < lv.zrem ? 1 : 0);
+    } else {
+        z0 = lv.off[tz - lv.nuni];
+        z1 = lv.off[tz - lv.nuni + 1];
+    }
+}
 cudaError_t launch_pm_stream(int cond, const CUtensorMap &tmap_in, float *out, int nx, int ny,
                              int nz, const Coef &k, const StreamPlan &plan,
                              unsigned long long *ctr, unsigned long long base, int *err,
@@ -107,16 +120,59 @@ cudaError_t simple_passes(const PassSeq &q);
 // Copy the last pass's result to out if it is not there already.
 cudaError_t passes_finish(const PassSeq &q);
 
+// ---- 2-byte depth-1 pass with 8 x 2 voxels per thread (pm_wide.cu) --------
+// 128 x (4 x consumer warps) column tiles, the same persistent-CTA / tile-counter / z-chunk
+// scheme as the streaming kernel (plan: pm_stream_plan with these tiles);
+// nx a multiple of 8, 16-byte aligned pointers.
+#ifndef AFD_WIDE_WARPS
+#define AFD_WIDE_WARPS 4  // consumer warps per CTA (each covers 4 rows)
+#endif
+#ifndef AFD_WIDE_SLOTS
+#define AFD_WIDE_SLOTS 8
+#endif
+#ifndef AFD_WIDE_CTAS
+#define AFD_WIDE_CTAS 3  // CTAs per SM the register cap is sized for
+#endif
+constexpr int kWideConsumerWarps = AFD_WIDE_WARPS;
+constexpr int kWideTX = 128;
+constexpr int kWideTY = 4 * kWideConsumerWarps;
+constexpr int kWideSlots = AFD_WIDE_SLOTS;
+constexpr int kWideThreads = kWideConsumerWarps * 32 + 32;
+// registers per thread for AFD_WIDE_CTAS CTAs per SM (the SM's four 16K
+// register quarters each hold a quarter of the warps, rounded up)
+constexpr int kWideWarpsPerQuarter = (AFD_WIDE_CTAS * (kWideThreads / 32) + 3) / 4;
+constexpr int kWideMaxRegs = 16384 / (32 * kWideWarpsPerQuarter) / 8 * 8 > 248
+                                 ? 248
+                                 : 16384 / (32 * kWideWarpsPerQuarter) / 8 * 8;
+// Shared-memory slot of the kernel per storage kind: one TMA box of the
+// largest tile shape the kernel is given (2-byte: 6400 bytes, float32:
+// 10752 bytes).
+constexpr int wide_slot_bytes(int S) { return S == 0 ? 10752 : 6400; }
+size_t pm_wide_smem_bytes(int S);
+// TMA box (elements, rows) of the single-cube tiles; x starts at x0 - 16/es
+void pm_wide_box(int S, int *box_w, int *box_h);
+// A batch cube's tile shape: tile columns of at most 128 voxels and equal
+// width (a multiple of 8), as many rows as the CTA's threads cover at that
+// width (within one slot): narrow cubes get one tall tile column.
+void pm_wide_shape(int S, int nx, int *tx, int *ty, int *tiles_x);
+cudaError_t pm_wide_prepare();
+cudaError_t pm_wide_occupancy(int *blocks_per_sm);
+cudaError_t launch_pm_wide(int S, int cond, const CUtensorMap &tmap_in, void *out, int nx, int ny,
+                           int nz, const Coef &k, const StreamPlan &plan, unsigned long long *ctr,
+                           unsigned long long base, int *err, cudaStream_t stream);
+
 // ---- a resident batch of cubes (streaming kernel over many cubes) ---------
 // Per-cube descriptor in device memory.  Roles: 0 input (resident), 1 result,
 // 2 scratch.  Rows are padded to `px` elements (a multiple of 16 bytes), which
 // is all the TMA needs, so any nx is streamed.
 struct BatchDesc {
-    CUtensorMap map[3];  // TMA descriptors of the three role buffers
-    void *buf[3];        // role buffers of this cube (storage format)
-    int64_t px;          // row pitch in elements
+    CUtensorMap map[3];   // TMA descriptors of the three role buffers (64 x 32 tiles)
+    CUtensorMap mapw[3];  // the same buffers with this cube's wide-kernel box
+    void *buf[3];         // role buffers of this cube (storage format)
+    int64_t px;           // row pitch in elements
     int nx, ny, nz;
     int tiles_x, tiles_y, zc;
+    int wtx, wty, wtiles_x, wtiles_y;  // wide-kernel tile shape and grid (pm_wide_shape)
     Coef coef;  // per-call coefficients, written on the device
     float K;    // K of the last call, value units
 };
@@ -129,6 +185,13 @@ cudaError_t launch_pm_batch(int S, int cond, const BatchDesc *desc, const int2 *
                             const int2 *roles, int64_t ntiles, int src_role, int dst_role, int grid,
                             unsigned long long *ctr, unsigned long long base, bool pdl, int *err,
                             cudaStream_t stream);
+
+// The same over the batch's per-cube wide tiles (pm_wide.cu): the list holds
+// (cube, tile) pairs numbered over each cube's wtiles_x x wtiles_y x z-chunks.
+cudaError_t launch_pm_wide_batch(int S, int cond, const BatchDesc *desc, const int2 *list,
+                                 const int2 *roles, int64_t ntiles, int src_role, int dst_role,
+                                 int grid, unsigned long long *ctr, unsigned long long base,
+                                 bool pdl, int *err, cudaStream_t stream);
 
 // ---- temporally blocked kernel (T iterations per pass, any storage) --------
 struct TbShape {

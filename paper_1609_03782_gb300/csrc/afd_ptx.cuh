@@ -92,6 +92,47 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
     }
 }
 
+// Bounded wait on an mbarrier given by its 32-bit shared-memory address, with
+// a suspend-time hint: a thread whose phase is not complete is suspended in
+// the try_wait itself (woken when the phase completes, or after hint_ns)
+// instead of spinning on issue slots that the CTA's working warps need.
+// Returns false (recording `code` in *err unless an earlier error is there)
+// after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity,
+                                                   uint32_t hint_ns)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, int *err, int code)
+{
+    constexpr uint32_t kHintNs = 100000;  // 0.1 ms per suspension
+    if (mbar_try_wait_hint(bar, parity, kHintNs))
+        return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_try_wait_hint(bar, parity, kHintNs))
+            return true;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive_u32(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // 3-D tiled TMA load of the box described by the tensor map into shared
 // memory, completing on `bar` (complete_tx).  The x coordinate times the
 // element size must be a multiple of 16 bytes; coordinates may be negative

@@ -186,12 +186,15 @@ cudaError_t batch_stats(int S, const BatchDesc *desc, const int64_t *len, int co
     }
 }
 
-// Tiles of every cube for z-chunk zc (0: 64 planes), in cube order, x
-// fastest, then stably sorted by chunk length, longest first: the tiles are
-// handed out dynamically in this order, so the last ones are the short
-// remainder chunks and the CTAs end close together.  Returns the z-chunk
-// used per cube through desc.
-std::vector<int2> build_tiles(std::vector<BatchDesc> &desc, int zc_req)
+// Tiles of every cube for z-chunk zc (0: 64 planes) under tile kind `kind`
+// (0: 64 x 32 tiles, 1: each cube's wide tiles), in cube order, x fastest,
+// then stably sorted by chunk length, longest first: the tiles are handed
+// out dynamically in this order, so the last ones are the short remainder
+// chunks and the CTAs end close together (the tiles of one cube's chunk stay
+// together, so neighbouring tiles run at the same time and share their halo
+// rows and columns through L2).  Returns the z-chunk used per cube through
+// desc.
+std::vector<int2> build_tiles(std::vector<BatchDesc> &desc, int zc_req, int kind)
 {
     std::vector<int2> list;
     std::vector<int> len;
@@ -203,7 +206,7 @@ std::vector<int2> build_tiles(std::vector<BatchDesc> &desc, int zc_req)
         if (zc > d.nz)
             zc = d.nz;
         d.zc = zc;
-        const int txy = d.tiles_x * d.tiles_y;
+        const int txy = kind ? d.wtiles_x * d.wtiles_y : d.tiles_x * d.tiles_y;
         const int nt = txy * ((d.nz + zc - 1) / zc);
         for (int t = 0; t < nt; ++t) {
             list.push_back(make_int2(static_cast<int>(c), t));
@@ -247,7 +250,7 @@ void free_batch(afd_batch *b)
 afd_status upload_tiles(afd_batch *b)
 {
     using namespace afd_host;
-    std::vector<int2> list = build_tiles(b->h_desc, b->zc);
+    std::vector<int2> list = build_tiles(b->h_desc, b->zc, b->tiles);
     if (b->d_list) {
         cudaFree(b->d_list);
         b->d_list = nullptr;
@@ -265,9 +268,7 @@ afd_status upload_tiles(afd_batch *b)
                        cudaMemcpyHostToDevice);
     if (e != cudaSuccess)
         return cuda_fail(b->ctx, e);
-    const int64_t gmax = static_cast<int64_t>(b->ctx->sm_count) * (b->ctx->stream_bps > 0
-                                                                       ? b->ctx->stream_bps
-                                                                       : 1);
+    const int64_t gmax = static_cast<int64_t>(b->ctx->sm_count) * batch_bps(b);
     b->grid = static_cast<int>(b->ntiles < gmax ? b->ntiles : gmax);
     if (b->exec) {  // the tile list is baked into the graph
         cudaGraphExecDestroy(b->exec);
@@ -306,6 +307,15 @@ afd_status afd_batch_create(afd_ctx *ctx, afd_batch **out, int count, const int6
             return cuda_fail(ctx, e);
         if (ctx->stream_bps < 1)
             ctx->stream_bps = 1;
+    }
+    if (ctx->wide_bps == 0) {
+        cudaError_t e = afd::pm_wide_prepare();
+        if (e == cudaSuccess)
+            e = afd::pm_wide_occupancy(&ctx->wide_bps);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e);
+        if (ctx->wide_bps < 1)
+            ctx->wide_bps = 1;
     }
     afd_batch *b = new (std::nothrow) afd_batch();
     if (!b)
@@ -353,10 +363,15 @@ afd_status afd_batch_create(afd_ctx *ctx, afd_batch **out, int count, const int6
         d.ny = static_cast<int>(b->ny[c]);
         d.nz = static_cast<int>(b->nz[c]);
         d.px = b->px[c];
+        afd::pm_wide_shape(storage, d.nx, &d.wtx, &d.wty, &d.wtiles_x);
+        d.wtiles_y = (d.ny + d.wty - 1) / d.wty;
         for (int r = 0; r < 3; ++r) {
             d.buf[r] = static_cast<char *>(b->arena[r]) + b->off[c] * es;
             st = encode_pitched_map(ctx, &d.map[r], d.buf[r], storage, box_w, box_h, d.nx, d.ny,
                                     d.nz, d.px);
+            if (st == AFD_OK)
+                st = encode_pitched_map(ctx, &d.mapw[r], d.buf[r], storage, d.wtx + 2 * (16 / es),
+                                        d.wty + 2, d.nx, d.ny, d.nz, d.px);
             if (st != AFD_OK) {
                 free_batch(b);
                 return st;
@@ -409,6 +424,18 @@ afd_status afd_batch_destroy(afd_batch *b)
     cudaStreamSynchronize(b->ctx->stream);
     free_batch(b);
     return AFD_OK;
+}
+
+afd_status afd_batch_set_tiles(afd_batch *b, int kind)
+{
+    if (!b || (kind != AFD_TILES_64X32 && kind != AFD_TILES_WIDE))
+        return AFD_EINVAL;
+    afd_status st = set_device(b->ctx);
+    if (st != AFD_OK)
+        return st;
+    cudaStreamSynchronize(b->ctx->stream);
+    b->tiles = kind;
+    return upload_tiles(b);
 }
 
 afd_status afd_batch_set_zchunk(afd_batch *b, int zc)
@@ -482,7 +509,7 @@ afd_status afd_batch_filter(afd_batch *b, const float *K, const float *spacing, 
                                           cond == AFD_COND_EXPONENTIAL, &kind);
     const bool same = b->exec && b->g_n == n_iter && b->g_cond == cond && b->g_kind == kind &&
                       b->g_dt == dt && b->g_h[0] == h[0] && b->g_h[1] == h[1] &&
-                      b->g_h[2] == h[2] && b->g_zc == b->zc;
+                      b->g_h[2] == h[2] && b->g_zc == b->zc && b->g_tiles == b->tiles;
     cudaError_t e = cudaSuccess;
     if (!same) {
         if (b->exec) {
@@ -509,11 +536,11 @@ afd_status afd_batch_filter(afd_batch *b, const float *K, const float *spacing, 
             for (int i = 0; i < n_iter && le == cudaSuccess; ++i) {
                 const int dst = ((n_iter - 1 - i) & 1) ? 2 : 1;
                 const int src = i == 0 ? 0 : (((n_iter - i) & 1) ? 2 : 1);
-                le = afd::launch_pm_batch(b->S, kind, b->d_desc, b->d_list, nullptr, b->ntiles, src, dst,
-                                          b->grid, ctx->d_tiles,
-                                          static_cast<unsigned long long>(i) *
-                                              static_cast<unsigned long long>(b->ntiles),
-                                          i > 0, ctx->d_err, b->cap);
+                le = batch_launch(b, kind, b->d_desc, b->d_list, nullptr, b->ntiles, src, dst,
+                                  b->grid, ctx->d_tiles,
+                                  static_cast<unsigned long long>(i) *
+                                      static_cast<unsigned long long>(b->ntiles),
+                                  i > 0, ctx->d_err, b->cap);
             }
             e = cudaStreamEndCapture(b->cap, &graph);
             if (e == cudaSuccess)
@@ -535,6 +562,7 @@ afd_status afd_batch_filter(afd_batch *b, const float *K, const float *spacing, 
         b->g_h[1] = h[1];
         b->g_h[2] = h[2];
         b->g_zc = b->zc;
+        b->g_tiles = b->tiles;
     }
     // K requests: through pinned staging, stream-ordered before the graph
     e = cudaStreamSynchronize(ctx->stream);  // the staging buffer may still be read

@@ -768,11 +768,12 @@ int guided_levels(int nz, int64_t txy, int64_t grid, int lmin, int *off)
 }
 }  // namespace
 
-StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_sm, int zc_hint)
+StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_sm, int zc_hint,
+                          int tile_x, int tile_y)
 {
     StreamPlan p;
-    p.tiles_x = (nx + TX - 1) / TX;
-    p.tiles_y = (ny + TY - 1) / TY;
+    p.tiles_x = (nx + tile_x - 1) / tile_x;
+    p.tiles_y = (ny + tile_y - 1) / tile_y;
     const int64_t txy = static_cast<int64_t>(p.tiles_x) * p.tiles_y;
     const int64_t gmax = static_cast<int64_t>(sm_count) * (blocks_per_sm > 0 ? blocks_per_sm : 1);
     ZLevels &lv = p.lv;

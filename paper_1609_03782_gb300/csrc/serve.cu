@@ -162,7 +162,7 @@ size_t cube_bytes(const afd_batch *b, int c)
 int64_t cube_tiles(const afd_batch *b, int c)
 {
     const afd::BatchDesc &d = b->h_desc[c];
-    return static_cast<int64_t>(d.tiles_x) * d.tiles_y * ((d.nz + d.zc - 1) / d.zc);
+    return batch_cube_txy(b, c) * ((d.nz + d.zc - 1) / d.zc);
 }
 
 // Retire rounds whose event has completed (all of them, waiting, if `all`).
@@ -212,9 +212,13 @@ afd_status admit(afd_serve *s)
         d = b->h_desc[q.cube];  // role 0: the resident cube
         d.buf[1] = static_cast<char *>(s->mem) + off;
         d.buf[2] = static_cast<char *>(s->mem) + off + half;
+        const int hxw = 16 / afd::store_bytes(b->S);
         for (int r = 1; r <= 2; ++r) {
             afd_status st = encode_pitched_map(s->ctx, &d.map[r], d.buf[r], b->S, box_w, box_h,
                                                d.nx, d.ny, d.nz, d.px);
+            if (st == AFD_OK)
+                st = encode_pitched_map(s->ctx, &d.mapw[r], d.buf[r], b->S, d.wtx + 2 * hxw,
+                                        d.wty + 2, d.nx, d.ny, d.nz, d.px);
             if (st != AFD_OK)
                 return st;
         }
@@ -273,15 +277,15 @@ afd_status launch_round(afd_serve *s, bool *launched)
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->d_list[p], list, n * sizeof(int2), cudaMemcpyHostToDevice, st);
-    const int64_t gmax = static_cast<int64_t>(s->ctx->sm_count) * s->ctx->stream_bps;
+    const int64_t gmax = static_cast<int64_t>(s->ctx->sm_count) * batch_bps(b);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
         if (!seg[k][1])
             continue;
         const int64_t nt = static_cast<int64_t>(seg[k][1]);
         const int64_t rounds = (nt + gmax - 1) / gmax;
         const int grid = static_cast<int>((nt + rounds - 1) / rounds);
-        e = afd::launch_pm_batch(b->S, k, s->d_desc, s->d_list[p] + seg[k][0], s->d_roles[p], nt,
-                                 0, 1, grid, nullptr, 0, false, s->ctx->d_err, st);
+        e = batch_launch(b, k, s->d_desc, s->d_list[p] + seg[k][0], s->d_roles[p], nt, 0, 1,
+                         grid, nullptr, 0, false, s->ctx->d_err, st);
         s->ctx->launches++;
     }
     if (e == cudaSuccess) {
@@ -315,9 +319,14 @@ afd_status afd_serve_create(afd_ctx *ctx, afd_batch *cubes, size_t mem_bytes, in
     s->ctx = ctx;
     s->cubes = cubes;
     s->cap = max_active;
+    // room for either tile kind (the batch's kind may change later)
     int64_t maxt = 0;
-    for (int c = 0; c < cubes->count; ++c)
-        maxt = std::max(maxt, cube_tiles(cubes, c));
+    for (int c = 0; c < cubes->count; ++c) {
+        const afd::BatchDesc &d = cubes->h_desc[c];
+        const int64_t chunks = (d.nz + d.zc - 1) / d.zc;
+        maxt = std::max(maxt, static_cast<int64_t>(d.tiles_x) * d.tiles_y * chunks);
+        maxt = std::max(maxt, static_cast<int64_t>(d.wtiles_x) * d.wtiles_y * chunks);
+    }
     s->list_cap = static_cast<size_t>(maxt) * max_active;
     const size_t dbytes = max_active * sizeof(afd::BatchDesc);
     const size_t rbytes = max_active * sizeof(int2);

@@ -1,10 +1,13 @@
 """Autotuner for the launch parameters that do not change results.
 
-Two knobs are tuned by timing, never by changing arithmetic (every kernel
+Three knobs are tuned by timing, never by changing arithmetic (every kernel
 variant is bit-identical):
 
 * the z-chunk of the streaming kernels (planes per tile), for a single cube
   (``afd_set_stream_zchunk``) or a resident batch (``afd_batch_set_zchunk``);
+* the tile shape of a resident batch (``afd_batch_set_tiles``): 64 x 32
+  tiles of 4 x 2 voxels per thread, or per-cube tiles of 8 x 2 voxels per
+  thread (tile columns of at most 128 voxels, as tall as the threads cover);
 * the temporal-blocking depth of ``afd_filter_ex`` (1, 2, 4 or 8).
 
 Results are cached in a JSON file keyed by what the choice depends on: the
@@ -22,6 +25,8 @@ import threading
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "afd_tune.json")
 ZCHUNKS = (0, 8, 16, 32, 64)
 DEPTHS = (1, 2, 4, 8)
+TILES = ("wide", "64x32")
+BATCH_ZCHUNKS = (16, 32, 64)
 
 
 def _bucket(v: int) -> int:
@@ -86,16 +91,22 @@ class Tuner:
 
     # -- the library's knobs ------------------------------------------------
     def tune_batch(self, afd, batch, K, dt, n_iter, conductance="rational", spacing=None,
-                   candidates=ZCHUNKS):
-        """Choose and apply the batch's z-chunk."""
+                   candidates=None):
+        """Choose and apply the batch's (tile kind, z-chunk); returns it."""
         key = batch_key(batch.shapes, batch.storage, conductance, n_iter)
+        if candidates is None:
+            candidates = [(t, z) for t in TILES for z in BATCH_ZCHUNKS]
 
-        def run(zc):
-            afd.afd_batch_set_zchunk(batch, zc)
+        def apply(c):
+            afd.afd_batch_set_tiles(batch, c[0])
+            afd.afd_batch_set_zchunk(batch, c[1])
+
+        def run(c):
+            apply(c)
             afd.afd_batch_filter(batch, K, dt, n_iter, conductance, spacing)
 
         best = self.pick(key, candidates, run)
-        afd.afd_batch_set_zchunk(batch, best)
+        apply(best)
         return best
 
     def tune_filter_ex(self, afd, ctx, src, dst, storage, scale, K, dt, n_iter,

@@ -51,7 +51,7 @@ def main(path):
     afd.afd_filter_intensity(ctx, src, out, 1.5, 1.0, 0.0325, 5, (5.0, 4.0, 3.0))
     step("intensity", out)
     # 2-byte storage and temporal blocking
-    for shape in [(17, 40, 196), (12, 16, 64)]:
+    for shape in [(17, 40, 196), (12, 16, 64), (9, 37, 264)]:
         src = cube(shape)
         for st, dt_ in (("f16", torch.float16), ("bf16", torch.bfloat16), ("i16", torch.int16)):
             q = torch.empty(shape, dtype=dt_, device="cuda")

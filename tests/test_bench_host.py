@@ -15,7 +15,9 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_ceilings_pick_the_lower_bound():
+def test_ceilings_pick_the_lower_bound(monkeypatch):
+    counts = {"f32/1": 29.9, "f16/1": 30.86, "i16/4": 43.0}
+    monkeypatch.setattr(bench, "figure", lambda section, key: counts.get(key))
     f32 = bench.ceilings("f32", 1, 780.0, 6786.2)
     assert f32["bound"] == "hbm"
     assert f32["hbm_ceiling"] == pytest.approx(6786.2 / 8.0)

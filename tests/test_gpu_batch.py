@@ -38,10 +38,12 @@ def shapes(count, seed):
     return out
 
 
-def test_batch_fp32_matches_alone_and_oracle(afd, ctx):
+@pytest.mark.parametrize("tiles", ["wide", "64x32"])
+def test_batch_fp32_matches_alone_and_oracle(afd, ctx, tiles):
     shp = shapes(14, 3)
     cubes = [synth.cutout(s, 50 + i) for i, s in enumerate(shp)]
     b = afd.afd_batch_create(ctx, shp, "f32")
+    afd.afd_batch_set_tiles(b, tiles)
     try:
         for i, c in enumerate(cubes):
             afd.afd_batch_set(b, i, torch.from_numpy(c).cuda())
@@ -79,27 +81,57 @@ def test_batch_fp32_matches_alone_and_oracle(afd, ctx):
         b.close()
 
 
+@pytest.mark.parametrize("tiles", ["wide", "64x32"])
+@pytest.mark.parametrize("storage", ["f16", "i16"])
 @pytest.mark.parametrize("cond", ["exponential", "rational"])
-def test_batch_f16_matches_alone(afd, ctx, cond):
-    shp = [(24, 40, 64), (17, 33, 77), (30, 64, 200), (5, 9, 11)]
+def test_batch_2byte_matches_alone(afd, ctx, cond, storage, tiles):
+    shp = [(24, 40, 64), (17, 33, 77), (30, 64, 200), (5, 9, 11), (9, 150, 33), (3, 2, 260)]
     cubes = [synth.cutout(s, 7 + i) for i, s in enumerate(shp)]
-    b = afd.afd_batch_create(ctx, shp, "f16", 1.0)
+    tdt = {"f16": torch.float16, "i16": torch.int16}[storage]
+    b = afd.afd_batch_create(ctx, shp, storage, 1.0)
+    afd.afd_batch_set_tiles(b, tiles)
     try:
         qs = []
         for i, c in enumerate(cubes):
-            q = torch.empty(shp[i], dtype=torch.float16, device="cuda")
-            afd.afd_quantize(ctx, torch.from_numpy(c).cuda(), q, "f16", 1.0)
+            q = torch.empty(shp[i], dtype=tdt, device="cuda")
+            afd.afd_quantize(ctx, torch.from_numpy(c).cuda(), q, storage, 1.0)
             qs.append(q)
             afd.afd_batch_set(b, i, q)
         afd.afd_batch_filter(b, [-1.5] * len(shp), 1 / 16, 7, cond, (1.0, 1.0, 0.5))
         Kused = afd.afd_batch_k(b)
         for i in range(len(shp)):
-            got = afd.afd_batch_get(b, i, torch.empty(shp[i], dtype=torch.float16, device="cuda"))
+            got = afd.afd_batch_get(b, i, torch.empty(shp[i], dtype=tdt, device="cuda"))
             ref = torch.empty_like(qs[i])
-            afd.afd_filter_ex(ctx, qs[i], ref, "f16", 1.0, float(Kused[i]), 1 / 16, 7, cond,
+            afd.afd_filter_ex(ctx, qs[i], ref, storage, 1.0, float(Kused[i]), 1 / 16, 7, cond,
                               (1.0, 1.0, 0.5), 1)
             afd.afd_sync(ctx)
             assert torch.equal(got.view(torch.int16), ref.view(torch.int16)), i
+    finally:
+        b.close()
+
+
+def test_batch_tile_kind_switch_keeps_bits(afd, ctx):
+    # the same batch filtered under both tile kinds, switching back and forth
+    shp = shapes(9, 11)
+    cubes = [synth.cutout(s, 90 + i) for i, s in enumerate(shp)]
+    b = afd.afd_batch_create(ctx, shp, "f32")
+    try:
+        for i, c in enumerate(cubes):
+            afd.afd_batch_set(b, i, torch.from_numpy(c).cuda())
+        res = {}
+        for kind in ("wide", "64x32", "wide"):
+            afd.afd_batch_set_tiles(b, kind)
+            afd.afd_batch_filter(b, [-1.5] * len(shp), 1 / 8, 9, "rational")
+            res.setdefault(kind, []).append(
+                [afd.afd_batch_get(b, i, torch.empty(shp[i], device="cuda")).clone()
+                 for i in range(len(shp))])
+        afd.afd_sync(ctx)
+        for i in range(len(shp)):
+            a = res["wide"][0][i].view(torch.int32)
+            assert torch.equal(a, res["64x32"][0][i].view(torch.int32)), i
+            assert torch.equal(a, res["wide"][1][i].view(torch.int32)), i
+        with pytest.raises(KeyError):
+            afd.afd_batch_set_tiles(b, "square")
     finally:
         b.close()
 

@@ -27,10 +27,11 @@ def ctx(afd):
 SHAPES = [(16, 40, 64), (9, 30, 45), (24, 64, 130), (5, 8, 8), (12, 33, 77)]
 
 
-@pytest.fixture(scope="module")
-def resident(afd, ctx):
+@pytest.fixture(scope="module", params=["wide", "64x32"])
+def resident(afd, ctx, request):
     cubes = []
     b = afd.afd_batch_create(ctx, SHAPES, "f16", 1.0)
+    afd.afd_batch_set_tiles(b, request.param)   # the service runs the batch's tile kind
     for i, s in enumerate(SHAPES):
         q = torch.empty(s, dtype=torch.float16, device="cuda")
         afd.afd_quantize(ctx, torch.from_numpy(synth.cutout(s, 90 + i)).cuda(), q, "f16", 1.0)

@@ -37,3 +37,37 @@ def test_keys_bucket_shapes():
     assert a != tune.shape_key("filter_ex", (256, 512, 512), "f32", "rational", 30)
     k = tune.batch_key([(32, 40, 50), (100, 100, 100)], "f32", "rational", 20)
     assert k.startswith("batch|2 cubes|")
+
+
+class _FakeAfd:
+    """Records the knob settings a tuner applies (no GPU)."""
+
+    def __init__(self, cost):
+        self.cost, self.state, self.calls = cost, {}, []
+
+    def afd_batch_set_tiles(self, b, kind):
+        self.state["tiles"] = kind
+
+    def afd_batch_set_zchunk(self, b, zc):
+        self.state["zc"] = zc
+
+    def afd_batch_filter(self, b, K, dt, n, cond, sp):
+        self.calls.append((self.state["tiles"], self.state["zc"]))
+
+
+def test_tune_batch_picks_tile_kind_and_zchunk(tmp_path):
+    cost = {(t, z): 10.0 for t in tune.TILES for z in tune.BATCH_ZCHUNKS}
+    cost[("64x32", 32)] = 3.0
+    fake = _FakeAfd(cost)
+
+    class B:
+        shapes = [(32, 40, 50), (64, 64, 64)]
+        storage = "f32"
+
+    t = tune.Tuner(str(tmp_path / "c.json"), timer=lambda fn, reps: (fn(), cost[fake.calls[-1]])[1])
+    best = t.tune_batch(fake, B(), [-1.5, -1.5], 0.125, 20)
+    assert best == ("64x32", 32)
+    assert fake.state == {"tiles": "64x32", "zc": 32}     # the choice is left applied
+    ms = json.loads((tmp_path / "c.json").read_text())[tune.batch_key(B.shapes, "f32",
+                                                                      "rational", 20)]["ms"]
+    assert any("wide" in k for k in ms) and any("64x32" in k for k in ms)
