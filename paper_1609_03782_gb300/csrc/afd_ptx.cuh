@@ -112,9 +112,12 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint32_t bar, uint32_t parity
     return ok != 0;
 }
 
+#ifndef AFD_WAIT_HINT_NS
+#define AFD_WAIT_HINT_NS 100000
+#endif
 __device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, int *err, int code)
 {
-    constexpr uint32_t kHintNs = 100000;  // 0.1 ms per suspension
+    constexpr uint32_t kHintNs = AFD_WAIT_HINT_NS;  // per suspension
     if (mbar_try_wait_hint(bar, parity, kHintNs))
         return true;
     const uint64_t t0 = globaltimer_ns();

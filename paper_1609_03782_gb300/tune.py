@@ -26,7 +26,7 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "afd_tune.json")
 ZCHUNKS = (0, 8, 16, 32, 64)
 DEPTHS = (1, 2, 4, 8)
 TILES = ("wide", "64x32")
-BATCH_ZCHUNKS = (16, 32, 64)
+BATCH_ZCHUNKS = (64, 32, 16)
 
 
 def _bucket(v: int) -> int:
