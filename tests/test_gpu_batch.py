@@ -82,12 +82,12 @@ def test_batch_fp32_matches_alone_and_oracle(afd, ctx, tiles):
 
 
 @pytest.mark.parametrize("tiles", ["wide", "64x32"])
-@pytest.mark.parametrize("storage", ["f16", "i16"])
+@pytest.mark.parametrize("storage", ["f16", "bf16", "i16"])
 @pytest.mark.parametrize("cond", ["exponential", "rational"])
 def test_batch_2byte_matches_alone(afd, ctx, cond, storage, tiles):
     shp = [(24, 40, 64), (17, 33, 77), (30, 64, 200), (5, 9, 11), (9, 150, 33), (3, 2, 260)]
     cubes = [synth.cutout(s, 7 + i) for i, s in enumerate(shp)]
-    tdt = {"f16": torch.float16, "i16": torch.int16}[storage]
+    tdt = {"f16": torch.float16, "bf16": torch.bfloat16, "i16": torch.int16}[storage]
     b = afd.afd_batch_create(ctx, shp, storage, 1.0)
     afd.afd_batch_set_tiles(b, tiles)
     try:
@@ -106,6 +106,32 @@ def test_batch_2byte_matches_alone(afd, ctx, cond, storage, tiles):
                               (1.0, 1.0, 0.5), 1)
             afd.afd_sync(ctx)
             assert torch.equal(got.view(torch.int16), ref.view(torch.int16)), i
+    finally:
+        b.close()
+
+
+@pytest.mark.parametrize("tiles", ["wide", "64x32"])
+def test_batch_heat_equation_limit(afd, ctx, tiles):
+    # K = +inf on every cube: the linear flux (g = 1), the discrete heat
+    # equation; each cube equal to the single-cube filter with K = +inf
+    shp = [(12, 30, 45), (20, 70, 129), (4, 5, 3)]
+    cubes = [synth.cutout(s, 31 + i) for i, s in enumerate(shp)]
+    b = afd.afd_batch_create(ctx, shp, "f32")
+    afd.afd_batch_set_tiles(b, tiles)
+    try:
+        for i, c in enumerate(cubes):
+            afd.afd_batch_set(b, i, torch.from_numpy(c).cuda())
+        afd.afd_batch_filter(b, [float("inf")] * len(shp), 0.1, 6, "rational")
+        for i, c in enumerate(cubes):
+            got = afd.afd_batch_get(b, i, torch.empty(shp[i], device="cuda"))
+            src = torch.from_numpy(c).cuda()
+            ref = torch.empty_like(src)
+            afd.afd_filter_out(ctx, src, ref, float("inf"), 0.1, 6, "rational")
+            afd.afd_sync(ctx)
+            assert torch.equal(got.view(torch.int32), ref.view(torch.int32)), i
+        o = oracle.pm_filter(cubes[1], float("inf"), 0.1, 6, "rational")
+        assert np.abs(afd.afd_batch_get(b, 1, torch.empty(shp[1], device="cuda")).cpu().numpy()
+                      - o).max() <= tol(6) * 10
     finally:
         b.close()
 
