@@ -123,3 +123,22 @@ def test_admission_by_memory(afd, ctx, resident):
             assert ei.value.status == afd.AFD_EINVAL
     finally:
         srv.close()
+
+
+def test_request_timestamps_are_ordered(afd, ctx, resident):
+    b, cubes = resident
+    srv = afd.afd_serve_create(b, 1 << 30, 8)
+    try:
+        t = afd.afd_serve_submit(srv, 2, 1.0, 0.125, 9, "rational")
+        sub, adm, first, done = afd.afd_serve_times(srv, t)
+        assert sub > 0 and adm == -1.0 and first == -1.0 and done == -1.0
+        drain(afd, srv, [t])
+        sub, adm, first, done = afd.afd_serve_times(srv, t)
+        assert 0 < sub <= adm <= first <= done, (sub, adm, first, done)
+        st, lat = afd.afd_serve_poll(srv, t)
+        assert st == 2 and abs(lat - (done - sub)) < 1e-9
+        afd.afd_serve_release(srv, t)
+        with pytest.raises(afd.AfdError):
+            afd.afd_serve_times(srv, t)          # released: unknown ticket
+    finally:
+        srv.close()
