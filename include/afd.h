@@ -100,8 +100,10 @@ afd_status afd_set_stream(afd_ctx *ctx, void *cuda_stream);
 /* Choose the kernel family used by afd_filter (default AFD_KERNEL_AUTO).
  * AFD_KERNEL_STREAM on a cube it cannot handle makes afd_filter return
  * AFD_EINVAL.  For afd_filter_ex's depth-1 passes on 2-byte storage, AUTO
- * runs the 8 x 2-voxel-per-thread streaming kernel and STREAM the 4 x 2 one.
- * All kernels give bit-identical results. */
+ * runs the 8 x 2-voxel-per-thread streaming kernel and STREAM the 4 x 2 one;
+ * for its depth-2 passes (nx a multiple of 8), AUTO runs the two-stage 8 x 2
+ * kernel and STREAM the general temporally blocked one.  All kernels give
+ * bit-identical results. */
 afd_status afd_set_kernel(afd_ctx *ctx, afd_kernel kernel);
 
 /* Tuning knob of the streaming kernel: the largest number of z planes one

@@ -23,9 +23,10 @@ SOURCES = ["afd_api.cu", "pm_simple.cu", "pm_stream.cu", "reduce.cu", "selftest.
            "noalloc.cu", "quant.cu", "tb_host.cu", "pm_tb_f32.cu", "pm_tb_f16.cu",
            "pm_tb_bf16.cu", "pm_tb_i16.cu", "pm_batch.cu",
            "serve.cu", "fdiag.cu", "smooth.cu", "smooth_direct.cu", "passes.cu",
-           "pm_wide.cu"]
+           "pm_wide.cu", "pm_wide2.cu"]
 HEADERS = ["afd_math.cuh", "afd_ptx.cuh", "afd_internal.h", "afd_store.cuh", "pm_tb.cuh",
-           "pm_tb_impl.cuh", "afd_ctx.h", "afd_batch.h", "afd_trace.h", "afd_check.cuh"]
+           "pm_tb_impl.cuh", "afd_ctx.h", "afd_batch.h", "afd_trace.h", "afd_check.cuh",
+           "pm_block.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no multiply/add contraction of scalar code anywhere; every FMA
 # the kernels want is written explicitly (afd_math.cuh also guards the packed

@@ -1333,6 +1333,43 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
             ctx->launches++;
             if (e != cudaSuccess)
                 return cuda_fail(ctx, e);
+        } else if (fits && T == 2 && nx % 8 == 0 && ctx->kernel != AFD_KERNEL_STREAM &&
+                   (kind == afd::COND_EXP || kind == afd::COND_RAT)) {
+            // depth 2: the two-stage 8 x 2-voxel kernel
+            if (ctx->wide2_bps == 0) {
+                e = afd::pm_wide2_prepare();
+                if (e == cudaSuccess)
+                    e = afd::pm_wide2_occupancy(&ctx->wide2_bps);
+                if (e != cudaSuccess)
+                    return cuda_fail(ctx, e);
+                if (ctx->wide2_bps < 1)
+                    ctx->wide2_bps = 1;
+            }
+            int bw = 0, bh = 0;
+            afd::pm_wide2_box(&bw, &bh);
+            CUtensorMap map;
+            st = encode_box_map(ctx, &map, src_of(i), S, bw, bh, static_cast<int>(nx),
+                                static_cast<int>(ny), static_cast<int>(nz));
+            if (st != AFD_OK)
+                return st;
+            afd::StreamPlan plan =
+                afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
+                                    static_cast<int>(nz), ctx->sm_count, ctx->wide2_bps,
+                                    ctx->zc_hint, afd::kWide2TX, afd::kWide2TY);
+            plan.pdl = prev_stream;
+            prev_stream = true;
+            if (!tiles_zeroed) {
+                e = tiles_reset(ctx);
+                tiles_zeroed = true;
+            }
+            if (e == cudaSuccess)
+                e = afd::launch_pm_wide2(S, kind, map, dst_of(i), static_cast<int>(nx),
+                                         static_cast<int>(ny), static_cast<int>(nz), k, plan,
+                                         ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream);
+            ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
+            ctx->launches++;
+            if (e != cudaSuccess)
+                return cuda_fail(ctx, e);
         } else if (fits) {
             if (!ctx->tb_ready[S][T]) {
                 e = afd::tb_prepare(S, T);

@@ -17,6 +17,7 @@ struct afd_ctx {
     int sm_count = 0;
     int stream_bps = 0;          // streaming kernel CTAs per SM (occupancy)
     int wide_bps = 0;            // 2-byte 8 x 2-voxel kernel CTAs per SM (occupancy)
+    int wide2_bps = 0;           // two-iteration float32 kernel CTAs per SM (occupancy)
     int zc_hint = 0;             // streaming kernel z-chunk override (0 = auto)
     afd_kernel kernel = AFD_KERNEL_AUTO;
     int *d_err = nullptr;        // device error word (bounded-wait expiries)

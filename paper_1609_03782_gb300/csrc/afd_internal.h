@@ -66,7 +66,7 @@ size_t pm_stream_smem_bytes();
 cudaError_t pm_stream_prepare();  // one-time kernel attributes
 cudaError_t pm_stream_occupancy(int *blocks_per_sm);
 StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_sm, int zc_hint,
-                          int tile_x = kStreamTX, int tile_y = kStreamTY);
+                          int tile_x = kStreamTX, int tile_y = kStreamTY, int zmax = 32);
 
 // The planes [z0, z1) of z-chunk tz of a plan's ZLevels.
 __host__ __device__ inline void zchunk(const ZLevels &lv, int tz, int &z0, int &z1)
@@ -160,6 +160,40 @@ cudaError_t pm_wide_occupancy(int *blocks_per_sm);
 cudaError_t launch_pm_wide(int S, int cond, const CUtensorMap &tmap_in, void *out, int nx, int ny,
                            int nz, const Coef &k, const StreamPlan &plan, unsigned long long *ctr,
                            unsigned long long base, int *err, cudaStream_t stream);
+
+// ---- two iterations per pass, 8 x 2 voxels per thread (pm_wide2.cu) ---------
+// afd_filter_ex's depth-2 passes, any storage kind.  128 x kWide2TY output
+// tiles; a TMA box of 144 x (kWide2TY + 4) elements around the tile (x
+// starts at x0 - 8, y at y0 - 2); nx a multiple of 8, 16-byte aligned
+// pointers.  Plan: pm_stream_plan with these tiles.
+#ifndef AFD_WIDE2_TY
+#define AFD_WIDE2_TY 24
+#endif
+#ifndef AFD_WIDE2_SLOTS
+#define AFD_WIDE2_SLOTS 4
+#endif
+#ifndef AFD_WIDE2_CTAS
+#define AFD_WIDE2_CTAS 1
+#endif
+constexpr int kWide2TX = 128;
+constexpr int kWide2TY = AFD_WIDE2_TY;
+// stage 2: one 8 x 2 block per thread over the tile; stage 1: one block per
+// thread over the tile grown by one voxel (17 x (TY/2 + 1) blocks)
+constexpr int kWide2S2Warps = (kWide2TX / 8) * (kWide2TY / 2) / 32;
+constexpr int kWide2S1Warps = ((kWide2TX / 8 + 1) * (kWide2TY / 2 + 1) + 31) / 32;
+constexpr int kWide2Slots = AFD_WIDE2_SLOTS;
+constexpr int kWide2Threads = (kWide2S1Warps + kWide2S2Warps + 1) * 32;  // + 1 producer warp
+constexpr int kWide2WarpsPerQuarter = (AFD_WIDE2_CTAS * (kWide2Threads / 32) + 3) / 4;
+constexpr int kWide2MaxRegs = 16384 / (32 * kWide2WarpsPerQuarter) / 8 * 8 > 248
+                                  ? 248
+                                  : 16384 / (32 * kWide2WarpsPerQuarter) / 8 * 8;
+void pm_wide2_box(int *box_w, int *box_h);
+cudaError_t pm_wide2_prepare();
+cudaError_t pm_wide2_occupancy(int *blocks_per_sm);
+cudaError_t launch_pm_wide2(int S, int cond, const CUtensorMap &tmap_in, void *out, int nx,
+                            int ny, int nz, const Coef &k, const StreamPlan &plan,
+                            unsigned long long *ctr, unsigned long long base, int *err,
+                            cudaStream_t stream);
 
 // ---- a resident batch of cubes (streaming kernel over many cubes) ---------
 // Per-cube descriptor in device memory.  Roles: 0 input (resident), 1 result,

@@ -24,13 +24,14 @@ cudaError_t stream_passes(const PassSeq &q, const CUtensorMap maps[3], const Str
                           unsigned long long *ctr, unsigned long long *base, int *err)
 {
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < q.n_iter && e == cudaSuccess; ++i) {
-        const float *src = pass_src(q.in, q.out, q.scratch, q.n_iter, i);
+    const int np = q.n_iter;
+    for (int i = 0; i < np && e == cudaSuccess; ++i) {
+        const float *src = pass_src(q.in, q.out, q.scratch, np, i);
         const int m = (src == q.in) ? 0 : (src == q.out ? 1 : 2);
         const afd_host::TraceRange pass_trace("pass");
         StreamPlan pl = plan;
         pl.pdl = i > 0;
-        e = launch_pm_stream(q.kind, maps[m], pass_dst(q.in, q.out, q.scratch, q.n_iter, i),
+        e = launch_pm_stream(q.kind, maps[m], pass_dst(q.in, q.out, q.scratch, np, i),
                              q.nx, q.ny, q.nz, q.k, pl, ctr, *base, err, q.stream);
         *base += static_cast<unsigned long long>(plan.ntiles);
         if (q.launches)
@@ -42,9 +43,10 @@ cudaError_t stream_passes(const PassSeq &q, const CUtensorMap maps[3], const Str
 cudaError_t simple_passes(const PassSeq &q)
 {
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < q.n_iter && e == cudaSuccess; ++i) {
-        e = launch_pm_simple(q.kind, pass_src(q.in, q.out, q.scratch, q.n_iter, i),
-                             pass_dst(q.in, q.out, q.scratch, q.n_iter, i), q.nx, q.ny, q.nz,
+    const int np = q.n_iter;
+    for (int i = 0; i < np && e == cudaSuccess; ++i) {
+        e = launch_pm_simple(q.kind, pass_src(q.in, q.out, q.scratch, np, i),
+                             pass_dst(q.in, q.out, q.scratch, np, i), q.nx, q.ny, q.nz,
                              q.k, q.stream);
         if (q.launches)
             ++*q.launches;

@@ -743,10 +743,10 @@ cudaError_t pm_stream_occupancy(int *blocks_per_sm)
 namespace {
 // Guided z-chunks: each chunk is at most the share of the remaining work that
 // keeps every CTA busy while the CTAs that took the chunk's tiles finish them
-// (length <= remaining x txy / (grid + txy)), between lmin and 32 planes; the
+// (length <= remaining x txy / (grid + txy)), between lmin and zmax planes; the
 // last chunks are the shortest, so the CTAs end within one short tile of each
 // other.  Returns the number of chunks (-1: more than kStreamMaxLevels).
-int guided_levels(int nz, int64_t txy, int64_t grid, int lmin, int *off)
+int guided_levels(int nz, int64_t txy, int64_t grid, int lmin, int *off, int zmax)
 {
     int n = 0, z = 0;
     while (z < nz) {
@@ -756,8 +756,8 @@ int guided_levels(int nz, int64_t txy, int64_t grid, int lmin, int *off)
         int64_t len = left * txy / (grid + txy);
         if (len < lmin)
             len = lmin;
-        if (len > 32)
-            len = 32;
+        if (len > zmax)
+            len = zmax;
         if (len > left || left - len < (lmin + 1) / 2)
             len = left;
         off[n++] = z;
@@ -769,7 +769,7 @@ int guided_levels(int nz, int64_t txy, int64_t grid, int lmin, int *off)
 }  // namespace
 
 StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_sm, int zc_hint,
-                          int tile_x, int tile_y)
+                          int tile_x, int tile_y, int zmax)
 {
     StreamPlan p;
     p.tiles_x = (nx + tile_x - 1) / tile_x;
@@ -785,7 +785,7 @@ StreamPlan pm_stream_plan(int nx, int ny, int nz, int sm_count, int blocks_per_s
     int n = -1;
     if (zc_hint <= 0)
         for (int lmin = 4; n < 0; lmin *= 2)
-            n = guided_levels(nz, txy, gmax, lmin, lv.off);
+            n = guided_levels(nz, txy, gmax, lmin, lv.off, zmax);
     if (n > 0) {
         lv.nlev = n;
         p.zc = 0;

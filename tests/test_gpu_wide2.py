@@ -1,0 +1,105 @@
+"""afd_filter_ex's depth-2 kernel (pm_wide2.cu: two stages of 8 x 2-voxel
+blocks, the default for widths that are a multiple of 8) against the general
+temporally blocked kernel of the same depth (afd_set_kernel 'stream'), bit for
+bit, for every storage format: both compute dequantise -> two canonical
+float32 iterations -> quantise, so any difference is a staging, halo,
+boundary or hand-over mistake.  With float32 storage a depth-2 pass also
+equals two single-iteration passes.  Shapes cover single planes, rows and
+columns, widths and heights at and around the 128 x 24 tile, odd iteration
+counts (a depth-1 pass at the end), both conductances with anisotropic
+spacing, int16 with a non-unit scale, in place and out of place, and forced
+z-chunks."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TDT = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16, "i16": torch.int16}
+RAW = {"f32": (torch.int32, np.int32), "f16": (torch.int16, np.uint16),
+       "bf16": (torch.int16, np.uint16), "i16": (torch.int16, np.int16)}
+SCALE = {"f32": 1.0, "f16": 1.0, "bf16": 1.0, "i16": 0.25}
+
+
+@pytest.fixture(scope="module")
+def ctx(afd):
+    c = afd.afd_create(0)
+    yield c
+    c.close()
+
+
+def stored(cube, storage):
+    """The cube in its storage format, on the device."""
+    if storage == "f32":
+        return torch.from_numpy(cube).cuda()
+    q = oracle.quantize(cube, storage, SCALE[storage])
+    return torch.from_numpy(np.ascontiguousarray(q).view(np.int16)).view(TDT[storage]).cuda()
+
+
+def run(afd, ctx, src, storage, K, dt, n, cond, sp, kernel, t_block=2, zc=0, inplace=False):
+    afd.afd_set_kernel(ctx, kernel)
+    afd.afd_set_stream_zchunk(ctx, zc)
+    try:
+        x = src.clone()
+        out = x if inplace else torch.empty_like(x)
+        afd.afd_filter_ex(ctx, x, out, storage, SCALE[storage], K, dt, n, cond, sp, t_block)
+        afd.afd_sync(ctx)
+    finally:
+        afd.afd_set_kernel(ctx, "auto")
+        afd.afd_set_stream_zchunk(ctx, 0)
+    tdt, ndt = RAW[storage]
+    return out.view(tdt).cpu().numpy().view(ndt)
+
+
+def cube(shape, seed):
+    rng = np.random.default_rng(seed)
+    c = (rng.standard_normal(shape) * 2.0).astype(np.float32)
+    c[tuple(s // 2 for s in shape)] = 9.0          # a bright voxel: large differences
+    return c
+
+
+SHAPES = [(1, 1, 8), (3, 2, 16), (2, 1, 136), (5, 33, 136), (17, 23, 128), (4, 24, 128),
+          (6, 25, 256), (40, 72, 264), (9, 49, 520), (4, 40, 8)]
+CASES = (("rational", None, 1.0, 1 / 8), ("exponential", (1.0, 1.5, 0.75), 1.3, 0.1))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16", "i16"])
+def test_depth2_equals_blocked_kernel(afd, ctx, shape, storage):
+    src = stored(cube(shape, sum(shape) + len(storage)), storage)
+    for cond, sp, K, dt in CASES:
+        for n in (2, 5):
+            a = run(afd, ctx, src, storage, K, dt, n, cond, sp, "auto")
+            b = run(afd, ctx, src, storage, K, dt, n, cond, sp, "stream")
+            assert np.array_equal(a, b), (cond, n, int((a != b).sum()))
+
+
+@pytest.mark.parametrize("shape", [(3, 2, 16), (17, 23, 128), (40, 72, 264)])
+def test_float32_depth2_equals_single_passes(afd, ctx, shape):
+    src = stored(cube(shape, 3 * sum(shape)), "f32")
+    for cond, sp, K, dt in CASES:
+        a = run(afd, ctx, src, "f32", K, dt, 6, cond, sp, "auto", t_block=2)
+        b = run(afd, ctx, src, "f32", K, dt, 6, cond, sp, "stream", t_block=1)
+        assert np.array_equal(a, b), cond
+
+
+@pytest.mark.parametrize("zc", [1, 3, 7])
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_depth2_zchunks_and_in_place(afd, ctx, zc, storage):
+    src = stored(cube((23, 45, 200), zc), storage)
+    ref = run(afd, ctx, src, storage, 1.0, 1 / 8, 4, "rational", None, "stream")
+    got = run(afd, ctx, src, storage, 1.0, 1 / 8, 4, "rational", None, "auto", zc=zc)
+    assert np.array_equal(got, ref)
+    got = run(afd, ctx, src, storage, 1.0, 1 / 8, 4, "rational", None, "auto", zc=zc,
+              inplace=True)
+    assert np.array_equal(got, ref)
+
+
+def test_depth2_against_oracle(afd, ctx):
+    c = cube((20, 37, 136), 5)
+    got = run(afd, ctx, stored(c, "f32"), "f32", 1.0, 0.125, 10, "rational", None, "auto")
+    ref = oracle.pm_filter(c, 1.0, 0.125, 10, "rational")
+    # float32 rounding of 10 iterations over values up to 9 (the bright voxel)
+    assert np.abs(got.view(np.float32) - ref).max() <= 4e-4
