@@ -175,6 +175,9 @@ cudaError_t launch_pm_wide(int S, int cond, const CUtensorMap &tmap_in, void *ou
 #ifndef AFD_WIDE2_CTAS
 #define AFD_WIDE2_CTAS 1
 #endif
+#ifndef AFD_WIDE2_P1
+#define AFD_WIDE2_P1 4
+#endif
 constexpr int kWide2TX = 128;
 constexpr int kWide2TY = AFD_WIDE2_TY;
 // stage 2: one 8 x 2 block per thread over the tile; stage 1: one block per
@@ -182,6 +185,7 @@ constexpr int kWide2TY = AFD_WIDE2_TY;
 constexpr int kWide2S2Warps = (kWide2TX / 8) * (kWide2TY / 2) / 32;
 constexpr int kWide2S1Warps = ((kWide2TX / 8 + 1) * (kWide2TY / 2 + 1) + 31) / 32;
 constexpr int kWide2Slots = AFD_WIDE2_SLOTS;
+constexpr int kWide2P1 = AFD_WIDE2_P1;  // stage-1 plane ring
 constexpr int kWide2Threads = (kWide2S1Warps + kWide2S2Warps + 1) * 32;  // + 1 producer warp
 constexpr int kWide2WarpsPerQuarter = (AFD_WIDE2_CTAS * (kWide2Threads / 32) + 3) / 4;
 constexpr int kWide2MaxRegs = 16384 / (32 * kWide2WarpsPerQuarter) / 8 * 8 > 248

@@ -60,7 +60,7 @@ constexpr uint32_t NIN = kWide2Slots;       // input ring
 constexpr int P1_W = TX2 + 8;               // stage-1 plane: x0 - 4 .. x0 + TX2 + 4
 constexpr int P1_H = TY2 + 2;               // y0 - 1 .. y0 + TY2 + 1
 constexpr int P1_SLOT = (P1_W * P1_H * 4 + 127) / 128 * 128;
-constexpr uint32_t NP1 = 4;                 // stage-1 plane ring
+constexpr uint32_t NP1 = kWide2P1;          // stage-1 plane ring
 static_assert((NIN & (NIN - 1)) == 0 && (NP1 & (NP1 - 1)) == 0, "ring sizes");
 static_assert((P1_W * 4) % 16 == 0, "16-byte rows");
 
