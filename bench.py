@@ -246,6 +246,21 @@ def pow2_near(v: float) -> float:
     return 2.0 ** math.floor(math.log2(v) + 0.5) if v > 0 and math.isfinite(v) else 1.0
 
 
+# the largest int16 count in units of the scale (AFD_I16FIX: counts of scale/1024)
+I16_RANGE = 32767.0 / 1024.0
+
+
+def i16_scale(max_abs: float) -> float:
+    """The finest power-of-two scale whose int16 range (I16_RANGE x scale)
+    holds max_abs.  The filter's result stays inside the input's range: each
+    explicit update is a convex combination of the voxel and its six
+    neighbours (the face weights dt g / h^2 sum to at most 6/8 < 1 with
+    g <= 1), so the filtered cube fits the same scale."""
+    if not (max_abs > 0 and math.isfinite(max_abs)):
+        return 1.0
+    return 2.0 ** math.ceil(math.log2(max_abs / I16_RANGE))
+
+
 class Issue:
     """Thread-instruction issue rate of the GPU: SMs x 4 schedulers x 32
     lanes x SM clock.  The SM count comes from the device, the clock from
@@ -311,8 +326,9 @@ def err_norms(got, ref, sig):
 
 
 def line_precision(afd, ctx, cube, d_in, ref32, sig):
-    """2-byte storage (per-cube power-of-two scale) x temporal depth on the
-    benchmark cube.  Errors are measured against the FP64 oracle on four
+    """2-byte storage (per-cube power-of-two scale: the one nearest the noise
+    rms for f16 and bf16, the finest that holds the cube's range for int16)
+    x temporal depth on the benchmark cube.  Errors are measured against the FP64 oracle on four
     sampled boxes (computed through the domain of dependence: exact), and,
     for context, against the float32 GPU result over the whole cube; in
     units of sigma.  gate: RMS and faint-band max within 1e-3 sigma."""
@@ -323,6 +339,7 @@ def line_precision(afd, ctx, cube, d_in, ref32, sig):
     K = K_SIGMA * sig
     Kf = float(np.float32(K))
     scale = pow2_near(sig)
+    scales = {"f16": scale, "bf16": scale, "i16": i16_scale(float(np.abs(cube).max()))}
     boxes = precision_boxes(cube)
     t0 = time.perf_counter()
     orc = [oracle.pm_filter_box(cube, bx, Kf, DT, N_ITER, COND) for bx in boxes]
@@ -353,18 +370,20 @@ def line_precision(afd, ctx, cube, d_in, ref32, sig):
         q = torch.empty(cube.shape, dtype=dt[st], device=d_in.device)
         o = torch.empty_like(q)
         back = torch.empty_like(d_in)
-        afd.afd_quantize(ctx, d_in, q, st, scale)
+        afd.afd_quantize(ctx, d_in, q, st, scales[st])
         for T in (1, 2, 4, 8):
-            run = lambda: afd.afd_filter_ex(ctx, q, o, st, scale, K, DT, N_ITER, COND, None, T)
+            run = lambda: afd.afd_filter_ex(ctx, q, o, st, scales[st], K, DT, N_ITER, COND, None,
+                                            T)
             run()
             ms = _events_ms(run, 5)
-            afd.afd_dequantize(ctx, o, back, st, scale)
+            afd.afd_dequantize(ctx, o, back, st, scales[st])
             afd.afd_sync(ctx)
             got = back.cpu().numpy()
             err = np.abs(got - ref)
             value = n_vox * N_ITER / (ms / 1e3) / 1e9
             eo = vs_oracle(got)
-            rows.append({"storage": st, "t_block": T, "ms": ms, "value": value,
+            rows.append({"storage": st, "scale": scales[st], "t_block": T, "ms": ms,
+                         "value": value,
                          "speedup_vs_f32": value / v32, "bytes_per_voxel_iter": 4.0 / T,
                          **ceilings(st, T, value, peak),
                          "err_vs_oracle": eo,
@@ -374,8 +393,10 @@ def line_precision(afd, ctx, cube, d_in, ref32, sig):
                                         "faint_max": float(err[faint].max()) / sig}})
         del q, o, back
     best = max(rows[1:], key=lambda r: r["value"])
-    return {"unit": UNIT, "scale": scale, "workload": "the headline cube, K = 1.0 sigma, "
-            "dt = 1/8, 50 rational iterations, stored in 2 bytes with a power-of-two scale; "
+    return {"unit": UNIT, "scale": scales, "workload": "the headline cube, K = 1.0 sigma, "
+            "dt = 1/8, 50 rational iterations, stored in 2 bytes with a power-of-two scale (f16, "
+            "bf16: the one nearest the noise rms; i16: the finest whose range, 32 x scale, holds "
+            "the cube's largest |I|); "
             "t_block iterations per pass over HBM (afd_filter_ex); err_vs_oracle: against the "
             "FP64 oracle on the float32 input over four 16x32x32 boxes %s (oracle through the "
             "domain of dependence, exact; %.1f s of oracle), in units of sigma (faint: |I| < 3 "

@@ -85,6 +85,16 @@ def test_summary_is_short_and_last():
     assert s["saturation_gvox_iter_per_s"] == 600.0
 
 
+def test_i16_scale_is_the_finest_that_holds_the_range():
+    # range 32767/1024 x scale = 31.999 x scale
+    assert bench.i16_scale(10.58) == 0.5          # 16.0 holds 10.58, 8.0 does not
+    assert bench.i16_scale(31.0) == 1.0
+    assert bench.i16_scale(32.5) == 2.0
+    assert bench.i16_scale(15.99) == 0.5
+    assert bench.i16_scale(16.0) == 1.0           # 0.5 gives 15.9995 < 16
+    assert bench.i16_scale(0.0) == 1.0 and bench.i16_scale(float("inf")) == 1.0
+
+
 def test_pow2_near():
     assert bench.pow2_near(1.0) == 1.0
     assert bench.pow2_near(0.9997) == 1.0
