@@ -274,13 +274,24 @@ class Issue:
         return cls.sm_count * 4 * 32 * cls.sm_mhz * 1e6
 
 
+def pass_bytes(storage: str, T: int) -> float:
+    """HBM bytes per voxel-iteration of afd_filter_ex at depth T (the
+    default kernels): one read and one write of the stored cube per pass at
+    depths 1 and 2; from depth 4 on, a chain of T/2 two-iteration launches
+    whose intermediate cubes are float32 (storage -> float32 -> ... ->
+    storage)."""
+    b = 4.0 if storage == "f32" else 2.0
+    if T <= 2:
+        return 2.0 * b / T
+    return (2.0 * b + 8.0 * (T // 2 - 1)) / T
+
+
 def ceilings(storage: str, T: int, value: float, peak_gbs: float):
     """HBM and issue ceilings (Gvox-it/s) of a pass, the one that binds, and
     the fraction of it reached.  The issue ceiling needs the pass's
     thread-instructions per voxel-iteration from an ncu capture of the
     current source (profiles/figures.json)."""
-    b = 4.0 if storage == "f32" else 2.0
-    hbm = peak_gbs / (2.0 * b / T)
+    hbm = peak_gbs / pass_bytes(storage, T)
     ins = figure("thread_instr_per_voxel_iter", "%s/%d" % (storage, T))
     issue = Issue.rate() / ins / 1e9 if ins else None
     bound = "issue" if issue is not None and issue < hbm else "hbm"
@@ -384,7 +395,8 @@ def line_precision(afd, ctx, cube, d_in, ref32, sig):
             eo = vs_oracle(got)
             rows.append({"storage": st, "scale": scales[st], "t_block": T, "ms": ms,
                          "value": value,
-                         "speedup_vs_f32": value / v32, "bytes_per_voxel_iter": 4.0 / T,
+                         "speedup_vs_f32": value / v32,
+                         "bytes_per_voxel_iter": pass_bytes(st, T),
                          **ceilings(st, T, value, peak),
                          "err_vs_oracle": eo,
                          "gate_pass": eo["rms"] <= GATE_SIGMA and eo["faint_max"] <= GATE_SIGMA,
@@ -397,8 +409,9 @@ def line_precision(afd, ctx, cube, d_in, ref32, sig):
             "dt = 1/8, 50 rational iterations, stored in 2 bytes with a power-of-two scale (f16, "
             "bf16: the one nearest the noise rms; i16: the finest whose range, 32 x scale, holds "
             "the cube's largest |I|); "
-            "t_block iterations per pass over HBM (afd_filter_ex); err_vs_oracle: against the "
-            "FP64 oracle on the float32 input over four 16x32x32 boxes %s (oracle through the "
+            "t_block iterations between roundings to the storage format (afd_filter_ex; "
+            "depths 4 and 8 as chains of two-iteration launches with float32 intermediate "
+            "cubes); err_vs_oracle: against the FP64 oracle on the float32 input over four 16x32x32 boxes %s (oracle through the "
             "domain of dependence, exact; %.1f s of oracle), in units of sigma (faint: |I| < 3 "
             "sigma); gate_pass: rms and faint max both <= 1e-3 sigma; err_vs_f32: against the "
             "float32 GPU result over the whole cube; per row the HBM ceiling (measured copy "

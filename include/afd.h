@@ -101,9 +101,9 @@ afd_status afd_set_stream(afd_ctx *ctx, void *cuda_stream);
  * AFD_KERNEL_STREAM on a cube it cannot handle makes afd_filter return
  * AFD_EINVAL.  For afd_filter_ex's depth-1 passes on 2-byte storage, AUTO
  * runs the 8 x 2-voxel-per-thread streaming kernel and STREAM the 4 x 2 one;
- * for its depth-2 passes (nx a multiple of 8), AUTO runs the two-stage 8 x 2
- * kernel and STREAM the general temporally blocked one.  All kernels give
- * bit-identical results. */
+ * for its passes of depth 2, 4 and 8 (nx a multiple of 8), AUTO runs chains
+ * of the two-stage 8 x 2 kernel and STREAM the general temporally blocked
+ * one.  All kernels give bit-identical results. */
 afd_status afd_set_kernel(afd_ctx *ctx, afd_kernel kernel);
 
 /* Tuning knob of the streaming kernel: the largest number of z planes one
@@ -250,7 +250,7 @@ afd_status afd_dequantize(afd_ctx *ctx, const void *in, float *out, int64_t n,
                           afd_storage storage, float scale);
 
 /* The filter on a cube in any storage format, with T = t_block iterations
- * fused per pass over HBM (temporal blocking).
+ * between roundings to the storage format (temporal blocking).
  *   in, out   DEVICE pointers to nx*ny*nz elements of `storage` (in == out
  *             filters in place; other overlaps are rejected).
  *   storage   AFD_F32, AFD_F16, AFD_BF16 or AFD_I16FIX.
@@ -265,11 +265,17 @@ afd_status afd_dequantize(afd_ctx *ctx, const void *in, float *out, int64_t n,
  * format; n_iter = (n_iter / T) passes of depth T, the remainder as passes
  * of depth 4, 2, 1 (at most T).  A pass is bit-identical to dequantise ->
  * that many afd_filter iterations -> quantise; with AFD_F32 the whole call
- * is bit-identical to afd_filter_out.  Bytes moved per voxel-iteration:
- * 2 * element size / T.  Uses one cube of context scratch in the storage
- * format (plus two float32 cubes when nx * element size is not a multiple of
- * 16 bytes, or K = +inf, where passes go through float32 scratch).
- * Asynchronous. */
+ * is bit-identical to afd_filter_out.  How a pass runs (afd_set_kernel):
+ * under AUTO, with nx a multiple of 8, a pass of depth T >= 2 is T/2
+ * launches of a two-iteration kernel whose intermediate cubes are float32
+ * (storage -> float32 -> ... -> storage: (2 b + 8 (T/2 - 1)) / T bytes per
+ * voxel-iteration for b-byte elements, e.g. 3 at depth 4 in 2 bytes; on
+ * GB300 these bytes cost less than the instructions of a deeper fused pass);
+ * under AFD_KERNEL_STREAM, or otherwise, one launch of the general blocked
+ * kernel (2 b / T bytes).  Uses one cube of context scratch in the
+ * storage format, plus two float32 cubes for passes of depth 4 or 8 under
+ * AUTO, or when nx * element size is not a multiple of 16 bytes or K = +inf
+ * (passes through float32 scratch).  Asynchronous. */
 afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage storage,
                          float scale, int64_t nx, int64_t ny, int64_t nz,
                          const float *spacing, float K, float dt, int n_iter,

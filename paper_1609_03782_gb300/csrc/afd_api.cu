@@ -490,6 +490,8 @@ afd_status afd_destroy(afd_ctx *ctx)
         cudaFree(ctx->fd_buf);
     if (ctx->lp_scratch)
         cudaFree(ctx->lp_scratch);
+    if (ctx->chain_f32)
+        cudaFree(ctx->chain_f32);
     if (ctx->fb_scratch)
         cudaFree(ctx->fb_scratch);
     for (cudaEvent_t ev : ctx->tev)
@@ -1333,9 +1335,11 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
             ctx->launches++;
             if (e != cudaSuccess)
                 return cuda_fail(ctx, e);
-        } else if (fits && T == 2 && nx % 8 == 0 && ctx->kernel != AFD_KERNEL_STREAM &&
+        } else if (fits && T >= 2 && nx % 8 == 0 && ctx->kernel != AFD_KERNEL_STREAM &&
                    (kind == afd::COND_EXP || kind == afd::COND_RAT)) {
-            // depth 2: the two-stage 8 x 2-voxel kernel
+            // depth T >= 2: T/2 launches of the two-stage 8 x 2-voxel kernel,
+            // storage -> float32 -> ... -> float32 -> storage: dequantise, T
+            // float32 iterations, quantise, as one blocked pass of depth T
             if (ctx->wide2_bps == 0) {
                 e = afd::pm_wide2_prepare();
                 if (e == cudaSuccess)
@@ -1345,31 +1349,49 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
                 if (ctx->wide2_bps < 1)
                     ctx->wide2_bps = 1;
             }
+            const int links = T / 2;
+            float *link_buf[2] = {nullptr, nullptr};
+            if (links > 1) {
+                const size_t fbytes = static_cast<size_t>(n) * sizeof(float);
+                st = ensure_buffer(ctx, &ctx->chain_f32, &ctx->chain_f32_bytes, 2 * fbytes);
+                if (st != AFD_OK)
+                    return st;
+                link_buf[0] = ctx->chain_f32;
+                link_buf[1] = ctx->chain_f32 + n;
+            }
             int bw = 0, bh = 0;
             afd::pm_wide2_box(&bw, &bh);
-            CUtensorMap map;
-            st = encode_box_map(ctx, &map, src_of(i), S, bw, bh, static_cast<int>(nx),
-                                static_cast<int>(ny), static_cast<int>(nz));
-            if (st != AFD_OK)
-                return st;
-            afd::StreamPlan plan =
+            const afd::StreamPlan plan0 =
                 afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
                                     static_cast<int>(nz), ctx->sm_count, ctx->wide2_bps,
                                     ctx->zc_hint, afd::kWide2TX, afd::kWide2TY);
-            plan.pdl = prev_stream;
-            prev_stream = true;
-            if (!tiles_zeroed) {
-                e = tiles_reset(ctx);
-                tiles_zeroed = true;
+            for (int l = 0; l < links; ++l) {
+                const int s_in = l == 0 ? S : afd::STORE_F32;
+                const int s_out = l == links - 1 ? S : afd::STORE_F32;
+                const void *lsrc = l == 0 ? src_of(i) : link_buf[(l - 1) & 1];
+                void *ldst = l == links - 1 ? dst_of(i) : link_buf[l & 1];
+                CUtensorMap map;
+                st = encode_box_map(ctx, &map, lsrc, s_in, bw, bh, static_cast<int>(nx),
+                                    static_cast<int>(ny), static_cast<int>(nz));
+                if (st != AFD_OK)
+                    return st;
+                afd::StreamPlan plan = plan0;
+                plan.pdl = prev_stream;
+                prev_stream = true;
+                if (!tiles_zeroed) {
+                    e = tiles_reset(ctx);
+                    tiles_zeroed = true;
+                }
+                if (e == cudaSuccess)
+                    e = afd::launch_pm_wide2(s_in, s_out, kind, map, ldst, static_cast<int>(nx),
+                                             static_cast<int>(ny), static_cast<int>(nz), k, plan,
+                                             ctx->d_tiles, ctx->tiles_base, ctx->d_err,
+                                             ctx->stream);
+                ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
+                ctx->launches++;
+                if (e != cudaSuccess)
+                    return cuda_fail(ctx, e);
             }
-            if (e == cudaSuccess)
-                e = afd::launch_pm_wide2(S, kind, map, dst_of(i), static_cast<int>(nx),
-                                         static_cast<int>(ny), static_cast<int>(nz), k, plan,
-                                         ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream);
-            ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
-            ctx->launches++;
-            if (e != cudaSuccess)
-                return cuda_fail(ctx, e);
         } else if (fits) {
             if (!ctx->tb_ready[S][T]) {
                 e = afd::tb_prepare(S, T);

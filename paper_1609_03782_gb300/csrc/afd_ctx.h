@@ -17,7 +17,7 @@ struct afd_ctx {
     int sm_count = 0;
     int stream_bps = 0;          // streaming kernel CTAs per SM (occupancy)
     int wide_bps = 0;            // 2-byte 8 x 2-voxel kernel CTAs per SM (occupancy)
-    int wide2_bps = 0;           // two-iteration float32 kernel CTAs per SM (occupancy)
+    int wide2_bps = 0;           // two-iteration kernel CTAs per SM (occupancy)
     int zc_hint = 0;             // streaming kernel z-chunk override (0 = auto)
     afd_kernel kernel = AFD_KERNEL_AUTO;
     int *d_err = nullptr;        // device error word (bounded-wait expiries)
@@ -39,6 +39,8 @@ struct afd_ctx {
     cudaStream_t d2h_stream = nullptr;  // device -> host copies
     float *lp_scratch = nullptr; // ping-pong partner of afd_filter_ex (any storage)
     size_t lp_scratch_bytes = 0;
+    float *chain_f32 = nullptr;  // two float32 cubes: the links of afd_filter_ex's deep passes
+    size_t chain_f32_bytes = 0;
     float *fb_scratch = nullptr; // float32 pair for the afd_filter_ex fallback
     size_t fb_scratch_bytes = 0;
     bool tb_ready[4][9] = {};    // tb_prepare done, per storage kind and depth

@@ -162,10 +162,12 @@ cudaError_t launch_pm_wide(int S, int cond, const CUtensorMap &tmap_in, void *ou
                            unsigned long long base, int *err, cudaStream_t stream);
 
 // ---- two iterations per pass, 8 x 2 voxels per thread (pm_wide2.cu) ---------
-// afd_filter_ex's depth-2 passes, any storage kind.  128 x kWide2TY output
-// tiles; a TMA box of 144 x (kWide2TY + 4) elements around the tile (x
-// starts at x0 - 8, y at y0 - 2); nx a multiple of 8, 16-byte aligned
-// pointers.  Plan: pm_stream_plan with these tiles.
+// afd_filter_ex's passes of depth 2 and more: input format S, output format
+// SO, either equal or one of them float32 (a chain 2-byte -> float32 -> ...
+// -> 2-byte is one pass of depth 2 x links).  128 x kWide2TY output tiles; a
+// TMA box of 144 x (kWide2TY + 4) input elements around the tile (x starts
+// at x0 - 8, y at y0 - 2); nx a multiple of 8, 16-byte aligned pointers.
+// Plan: pm_stream_plan with these tiles.
 #ifndef AFD_WIDE2_TY
 #define AFD_WIDE2_TY 24
 #endif
@@ -194,8 +196,8 @@ constexpr int kWide2MaxRegs = 16384 / (32 * kWide2WarpsPerQuarter) / 8 * 8 > 248
 void pm_wide2_box(int *box_w, int *box_h);
 cudaError_t pm_wide2_prepare();
 cudaError_t pm_wide2_occupancy(int *blocks_per_sm);
-cudaError_t launch_pm_wide2(int S, int cond, const CUtensorMap &tmap_in, void *out, int nx,
-                            int ny, int nz, const Coef &k, const StreamPlan &plan,
+cudaError_t launch_pm_wide2(int S, int SO, int cond, const CUtensorMap &tmap_in, void *out,
+                            int nx, int ny, int nz, const Coef &k, const StreamPlan &plan,
                             unsigned long long *ctr, unsigned long long base, int *err,
                             cudaStream_t stream);
 

@@ -1,12 +1,16 @@
 // Two explicit per-face Perona-Malik iterations per pass (temporal blocking;
 // arXiv:1609.03782 Sec. 3.3, the per-face discretisation of eq. "perona"
-// with the gradient conductance, evaluated twice per HBM pass), for float32
-// or 2-byte storage.  A pass reads the cube once and writes it once for two
-// iterations.  Every value is the canonical per-face arithmetic
-// (afd_math.cuh) and the intermediate iteration stays float32, so a pass
-// equals dequantise -> two float32 iterations -> quantise, bit for bit the
-// temporally blocked kernel of the same depth (pm_tb.cuh), and with float32
-// storage two single-iteration passes.
+// with the gradient conductance, evaluated twice per HBM pass), from an
+// input in format SI to an output in format SO (float32 or 2-byte storage).
+// A pass reads the cube once and writes it once for two iterations.  Every
+// value is the canonical per-face arithmetic (afd_math.cuh) and the
+// intermediate iteration stays float32, so a pass equals dequantise -> two
+// float32 iterations -> quantise, bit for bit the temporally blocked kernel
+// of the same depth (pm_tb.cuh), and with float32 storage two
+// single-iteration passes.  A chain SI -> float32 -> ... -> float32 -> SO of
+// these passes is therefore T = 2 x (links) float32 iterations between one
+// dequantisation and one quantisation: the temporally blocked kernel of
+// depth T, bit for bit.
 //
 // Design (sm_103a), per persistent CTA (TY = kWide2TY output rows):
 //   * The last warp is the TMA producer: for a 128 x TY output tile and a
@@ -20,7 +24,7 @@
 //     memory.  With 2-byte storage its rows start 8 bytes into a 16-byte
 //     word, so they are read as two 8-byte loads.
 //   * Stage 2 (the next kWide2S2Warps warps): the second iteration over the
-//     tile from those planes, rounded to the storage format and stored to
+//     tile from those planes, rounded to the output format and stored to
 //     global memory.
 //   * The stages hand planes over through mbarriers (full / empty per ring
 //     plane), so neither waits for the other except on the data itself.
@@ -207,12 +211,12 @@ __device__ __forceinline__ void sts8x2(unsigned char *p, int pitch_b, const f2_t
     q1[1] = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
-template <int S, int C>
+template <int S, int SO, int C>
 __global__ void __maxnreg__(kWide2MaxRegs)
-    pm_step_wide2(const __grid_constant__ CUtensorMap tmap, typename Store<S>::T *__restrict__ out,
-                  int nx, int ny, int nz, int tiles_x, int txy,
-                  const __grid_constant__ ZLevels lv, int ntiles, unsigned long long *ctr,
-                  unsigned long long base, Coef kc, int *err)
+    pm_step_wide2(const __grid_constant__ CUtensorMap tmap,
+                  typename Store<SO>::T *__restrict__ out, int nx, int ny, int nz, int tiles_x,
+                  int txy, const __grid_constant__ ZLevels lv, int ntiles,
+                  unsigned long long *ctr, unsigned long long base, Coef kc, int *err)
 {
     typedef In<S> IS;
     grid_dep_launch_dependents();  // the next pass may take SMs as this one frees them
@@ -386,7 +390,7 @@ __global__ void __maxnreg__(kWide2MaxRegs)
                              check_range(err, w.y0, 0, ny, kChkStreamTile);
         const bool act0 = tile_ok && x < nx && ya < ny;
         const bool act1 = tile_ok && x < nx && yb < ny;
-        typename Store<S>::T *po = out + (static_cast<int64_t>(w.z0) * ny + ya) * nx + x;
+        typename Store<SO>::T *po = out + (static_cast<int64_t>(w.z0) * ny + ya) * nx + x;
         const uint32_t kb2 = k2;
         uint32_t r = kb2 + static_cast<uint32_t>(w.z0 - zlo1);
         f2_t c0[4], c1[4], fb0[4], fb1[4];
@@ -415,10 +419,10 @@ __global__ void __maxnreg__(kWide2MaxRegs)
         if (!stage_step<STORE_F32, C, false>(p1, o, k, r, z + 1 < nz, false, 0, 8, C0, C1, FB0, \
                                              FB1, N0, N1, FA0, FA1, o0, o1))                   \
             return;                                                                            \
-        stg8<S>(po, o0,                                                                        \
-                act0 && check_range(err, po - out, 0, nz * plane - 7, kChkStreamStore));       \
-        stg8<S>(po + nx, o1,                                                                   \
-                act1 && check_range(err, po + nx - out, 0, nz * plane - 7, kChkStreamStore));  \
+        stg8<SO>(po, o0,                                                                       \
+                 act0 && check_range(err, po - out, 0, nz * plane - 7, kChkStreamStore));      \
+        stg8<SO>(po + nx, o1,                                                                  \
+                 act1 && check_range(err, po + nx - out, 0, nz * plane - 7, kChkStreamStore)); \
         po += plane;                                                                           \
         ++r;                                                                                   \
         ++z;                                                                                   \
@@ -443,7 +447,7 @@ size_t smem_bytes2()
            2 * (NIN + NP1) * sizeof(uint64_t) + (NIN + NP1) * sizeof(int) + 128;
 }
 
-template <int S, int C>
+template <int S, int SO, int C>
 cudaError_t wide2_launch(const CUtensorMap &tmap, void *out, int nx, int ny, int nz,
                          const Coef &k, const StreamPlan &plan, unsigned long long *ctr,
                          unsigned long long base, int *err, cudaStream_t stream)
@@ -460,38 +464,75 @@ cudaError_t wide2_launch(const CUtensorMap &tmap, void *out, int nx, int ny, int
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = plan.pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, pm_step_wide2<S, C>, tmap,
-                              static_cast<typename Store<S>::T *>(out), nx, ny, nz, plan.tiles_x,
+    return cudaLaunchKernelEx(&cfg, pm_step_wide2<S, SO, C>, tmap,
+                              static_cast<typename Store<SO>::T *>(out), nx, ny, nz, plan.tiles_x,
                               plan.tiles_x * plan.tiles_y, plan.lv, static_cast<int>(plan.ntiles),
                               ctr, base, k, err);
 }
 
-template <int S>
-cudaError_t prepare_s()
+template <int S, int SO>
+cudaError_t prepare_pair()
 {
     const int smem = static_cast<int>(smem_bytes2<S>());
-    cudaError_t e = cudaFuncSetAttribute(pm_step_wide2<S, COND_EXP>,
+    cudaError_t e = cudaFuncSetAttribute(pm_step_wide2<S, SO, COND_EXP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(pm_step_wide2<S, COND_RAT>,
+        e = cudaFuncSetAttribute(pm_step_wide2<S, SO, COND_RAT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
-template <int S>
-cudaError_t launch_s(int cond, const CUtensorMap &tmap, void *out, int nx, int ny, int nz,
-                     const Coef &k, const StreamPlan &plan, unsigned long long *ctr,
-                     unsigned long long base, int *err, cudaStream_t stream)
+template <int S, int SO>
+cudaError_t launch_pair(int cond, const CUtensorMap &tmap, void *out, int nx, int ny, int nz,
+                        const Coef &k, const StreamPlan &plan, unsigned long long *ctr,
+                        unsigned long long base, int *err, cudaStream_t stream)
 {
     switch (cond) {
     case COND_EXP:
-        return wide2_launch<S, COND_EXP>(tmap, out, nx, ny, nz, k, plan, ctr, base, err, stream);
+        return wide2_launch<S, SO, COND_EXP>(tmap, out, nx, ny, nz, k, plan, ctr, base, err,
+                                             stream);
     case COND_RAT:
-        return wide2_launch<S, COND_RAT>(tmap, out, nx, ny, nz, k, plan, ctr, base, err, stream);
+        return wide2_launch<S, SO, COND_RAT>(tmap, out, nx, ny, nz, k, plan, ctr, base, err,
+                                             stream);
     default:
         return cudaErrorInvalidValue;  // the other conductance kinds have no depth-2 pass
     }
 }
+
+// A 2-byte format to and from float32, and to itself
+template <int S>
+cudaError_t prepare_s()
+{
+    cudaError_t e = prepare_pair<S, S>();
+    if (e == cudaSuccess)
+        e = prepare_pair<S, STORE_F32>();
+    if (e == cudaSuccess)
+        e = prepare_pair<STORE_F32, S>();
+    return e;
+}
+
+template <int S>
+cudaError_t launch_s(int SO, int cond, const CUtensorMap &tmap, void *out, int nx, int ny, int nz,
+                     const Coef &k, const StreamPlan &plan, unsigned long long *ctr,
+                     unsigned long long base, int *err, cudaStream_t stream)
+{
+    if (SO == S)
+        return launch_pair<S, S>(cond, tmap, out, nx, ny, nz, k, plan, ctr, base, err, stream);
+    if (SO == STORE_F32)
+        return launch_pair<S, STORE_F32>(cond, tmap, out, nx, ny, nz, k, plan, ctr, base, err,
+                                         stream);
+    return cudaErrorInvalidValue;
+}
+
+template <int SO>
+cudaError_t launch_from_f32(int cond, const CUtensorMap &tmap, void *out, int nx, int ny, int nz,
+                            const Coef &k, const StreamPlan &plan, unsigned long long *ctr,
+                            unsigned long long base, int *err, cudaStream_t stream)
+{
+    return launch_pair<STORE_F32, SO>(cond, tmap, out, nx, ny, nz, k, plan, ctr, base, err,
+                                      stream);
+}
+
 
 }  // namespace
 
@@ -503,7 +544,7 @@ void pm_wide2_box(int *box_w, int *box_h)
 
 cudaError_t pm_wide2_prepare()
 {
-    cudaError_t e = prepare_s<STORE_F32>();
+    cudaError_t e = prepare_pair<STORE_F32, STORE_F32>();
     if (e == cudaSuccess)
         e = prepare_s<STORE_F16>();
     if (e == cudaSuccess)
@@ -515,28 +556,44 @@ cudaError_t pm_wide2_prepare()
 
 cudaError_t pm_wide2_occupancy(int *blocks_per_sm)
 {
-    // float32 slots are the largest: its occupancy bounds every format's
+    // float32 input slots are the largest: its occupancy bounds every pair's
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks_per_sm, pm_step_wide2<STORE_F32, COND_RAT>, kWide2Threads,
+        blocks_per_sm, pm_step_wide2<STORE_F32, STORE_F32, COND_RAT>, kWide2Threads,
         smem_bytes2<STORE_F32>());
 }
 
-cudaError_t launch_pm_wide2(int S, int cond, const CUtensorMap &tmap_in, void *out, int nx,
-                            int ny, int nz, const Coef &k, const StreamPlan &plan,
+cudaError_t launch_pm_wide2(int S, int SO, int cond, const CUtensorMap &tmap_in, void *out,
+                            int nx, int ny, int nz, const Coef &k, const StreamPlan &plan,
                             unsigned long long *ctr, unsigned long long base, int *err,
                             cudaStream_t stream)
 {
     switch (S) {
-    case STORE_F32:
-        return launch_s<STORE_F32>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base, err, stream);
     case STORE_F16:
-        return launch_s<STORE_F16>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base, err, stream);
+        return launch_s<STORE_F16>(SO, cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base, err,
+                                   stream);
     case STORE_BF16:
-        return launch_s<STORE_BF16>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base, err,
+        return launch_s<STORE_BF16>(SO, cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base, err,
                                     stream);
-    default:
-        return launch_s<STORE_I16>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base, err, stream);
+    case STORE_I16:
+        return launch_s<STORE_I16>(SO, cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base, err,
+                                   stream);
+    case STORE_F32:
+        switch (SO) {
+        case STORE_F32:
+            return launch_from_f32<STORE_F32>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base,
+                                              err, stream);
+        case STORE_F16:
+            return launch_from_f32<STORE_F16>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base,
+                                              err, stream);
+        case STORE_BF16:
+            return launch_from_f32<STORE_BF16>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base,
+                                               err, stream);
+        case STORE_I16:
+            return launch_from_f32<STORE_I16>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base,
+                                              err, stream);
+        }
     }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace afd

@@ -1,14 +1,15 @@
-"""afd_filter_ex's depth-2 kernel (pm_wide2.cu: two stages of 8 x 2-voxel
-blocks, the default for widths that are a multiple of 8) against the general
-temporally blocked kernel of the same depth (afd_set_kernel 'stream'), bit for
-bit, for every storage format: both compute dequantise -> two canonical
-float32 iterations -> quantise, so any difference is a staging, halo,
-boundary or hand-over mistake.  With float32 storage a depth-2 pass also
-equals two single-iteration passes.  Shapes cover single planes, rows and
-columns, widths and heights at and around the 128 x 24 tile, odd iteration
-counts (a depth-1 pass at the end), both conductances with anisotropic
-spacing, int16 with a non-unit scale, in place and out of place, and forced
-z-chunks."""
+"""afd_filter_ex's passes of depth 2, 4 and 8 on the two-iteration kernel
+(pm_wide2.cu: two stages of 8 x 2-voxel blocks; depth T as T/2 launches with
+float32 intermediate cubes; the default for widths that are a multiple of 8)
+against the general temporally blocked kernel of the same depth
+(afd_set_kernel 'stream'), bit for bit, for every storage format: both
+compute dequantise -> T canonical float32 iterations -> quantise, so any
+difference is a staging, halo, boundary, hand-over or chaining mistake.  With
+float32 storage a pass also equals single-iteration passes.  Shapes cover
+single planes, rows and columns, widths and heights at and around the
+128 x 24 tile, iteration counts with a remainder (shallower passes at the
+end), both conductances with anisotropic spacing, int16 with a non-unit
+scale, in place and out of place, and forced z-chunks."""
 import numpy as np
 import pytest
 
@@ -65,41 +66,47 @@ SHAPES = [(1, 1, 8), (3, 2, 16), (2, 1, 136), (5, 33, 136), (17, 23, 128), (4, 2
 CASES = (("rational", None, 1.0, 1 / 8), ("exponential", (1.0, 1.5, 0.75), 1.3, 0.1))
 
 
+@pytest.mark.parametrize("T", [2, 4, 8])
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16", "i16"])
-def test_depth2_equals_blocked_kernel(afd, ctx, shape, storage):
-    src = stored(cube(shape, sum(shape) + len(storage)), storage)
+def test_depth_equals_blocked_kernel(afd, ctx, shape, storage, T):
+    src = stored(cube(shape, sum(shape) + len(storage) + T), storage)
     for cond, sp, K, dt in CASES:
-        for n in (2, 5):
-            a = run(afd, ctx, src, storage, K, dt, n, cond, sp, "auto")
-            b = run(afd, ctx, src, storage, K, dt, n, cond, sp, "stream")
+        for n in (T, 2 * T - 1):
+            a = run(afd, ctx, src, storage, K, dt, n, cond, sp, "auto", t_block=T)
+            b = run(afd, ctx, src, storage, K, dt, n, cond, sp, "stream", t_block=T)
             assert np.array_equal(a, b), (cond, n, int((a != b).sum()))
 
 
+@pytest.mark.parametrize("T", [2, 4, 8])
 @pytest.mark.parametrize("shape", [(3, 2, 16), (17, 23, 128), (40, 72, 264)])
-def test_float32_depth2_equals_single_passes(afd, ctx, shape):
+def test_float32_depth_equals_single_passes(afd, ctx, shape, T):
     src = stored(cube(shape, 3 * sum(shape)), "f32")
     for cond, sp, K, dt in CASES:
-        a = run(afd, ctx, src, "f32", K, dt, 6, cond, sp, "auto", t_block=2)
-        b = run(afd, ctx, src, "f32", K, dt, 6, cond, sp, "stream", t_block=1)
-        assert np.array_equal(a, b), cond
+        a = run(afd, ctx, src, "f32", K, dt, 2 * T, cond, sp, "auto", t_block=T)
+        b = run(afd, ctx, src, "f32", K, dt, 2 * T, cond, sp, "stream", t_block=1)
+        assert np.array_equal(a, b), (cond, T)
 
 
+@pytest.mark.parametrize("T", [2, 4])
 @pytest.mark.parametrize("zc", [1, 3, 7])
 @pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_depth2_zchunks_and_in_place(afd, ctx, zc, storage):
+def test_depth_zchunks_and_in_place(afd, ctx, zc, storage, T):
     src = stored(cube((23, 45, 200), zc), storage)
-    ref = run(afd, ctx, src, storage, 1.0, 1 / 8, 4, "rational", None, "stream")
-    got = run(afd, ctx, src, storage, 1.0, 1 / 8, 4, "rational", None, "auto", zc=zc)
+    ref = run(afd, ctx, src, storage, 1.0, 1 / 8, 2 * T, "rational", None, "stream", t_block=T)
+    got = run(afd, ctx, src, storage, 1.0, 1 / 8, 2 * T, "rational", None, "auto", t_block=T,
+              zc=zc)
     assert np.array_equal(got, ref)
-    got = run(afd, ctx, src, storage, 1.0, 1 / 8, 4, "rational", None, "auto", zc=zc,
-              inplace=True)
+    got = run(afd, ctx, src, storage, 1.0, 1 / 8, 2 * T, "rational", None, "auto", t_block=T,
+              zc=zc, inplace=True)
     assert np.array_equal(got, ref)
 
 
-def test_depth2_against_oracle(afd, ctx):
+@pytest.mark.parametrize("T", [2, 4, 8])
+def test_depth_against_oracle(afd, ctx, T):
     c = cube((20, 37, 136), 5)
-    got = run(afd, ctx, stored(c, "f32"), "f32", 1.0, 0.125, 10, "rational", None, "auto")
+    got = run(afd, ctx, stored(c, "f32"), "f32", 1.0, 0.125, 10, "rational", None, "auto",
+              t_block=T)
     ref = oracle.pm_filter(c, 1.0, 0.125, 10, "rational")
     # float32 rounding of 10 iterations over values up to 9 (the bright voxel)
     assert np.abs(got.view(np.float32) - ref).max() <= 4e-4
