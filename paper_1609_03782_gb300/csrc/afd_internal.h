@@ -169,7 +169,7 @@ cudaError_t launch_pm_wide(int S, int cond, const CUtensorMap &tmap_in, void *ou
 // at x0 - 8, y at y0 - 2); nx a multiple of 8, 16-byte aligned pointers.
 // Plan: pm_stream_plan with these tiles.
 #ifndef AFD_WIDE2_TY
-#define AFD_WIDE2_TY 24
+#define AFD_WIDE2_TY 28  // 8 stage-1 + 7 stage-2 + 1 producer warps: 16 x 32 x 128 registers
 #endif
 #ifndef AFD_WIDE2_SLOTS
 #define AFD_WIDE2_SLOTS 4
