@@ -145,9 +145,20 @@ constexpr int kWideMaxRegs = 16384 / (32 * kWideWarpsPerQuarter) / 8 * 8 > 248
                                  ? 248
                                  : 16384 / (32 * kWideWarpsPerQuarter) / 8 * 8;
 // Shared-memory slot of the kernel per storage kind: one TMA box of the
-// largest tile shape the kernel is given (2-byte: 6400 bytes, float32:
-// 10752 bytes).
-constexpr int wide_slot_bytes(int S) { return S == 0 ? 10752 : 6400; }
+// largest tile shape the kernel is given.
+constexpr int wide_slot_round(int b) { return (b + 127) / 128 * 128; }
+constexpr int wide_slot_bytes(int S)
+{
+    // at least the single-cube box (the tile, a one-row y halo, a 16-byte x
+    // halo); no less than 10752 / 6400 bytes, so narrow batch cubes get tall
+    // tiles
+    return S == 0 ? (wide_slot_round((kWideTX + 8) * (kWideTY + 2) * 4) > 10752
+                         ? wide_slot_round((kWideTX + 8) * (kWideTY + 2) * 4)
+                         : 10752)
+                  : (wide_slot_round((kWideTX + 16) * (kWideTY + 2) * 2) > 6400
+                         ? wide_slot_round((kWideTX + 16) * (kWideTY + 2) * 2)
+                         : 6400);
+}
 size_t pm_wide_smem_bytes(int S);
 // TMA box (elements, rows) of the single-cube tiles; x starts at x0 - 16/es
 void pm_wide_box(int S, int *box_w, int *box_h);
