@@ -136,6 +136,30 @@ __device__ __forceinline__ Offs block_offs(int x, int ya, int nx, int ny, int x_
     return o;
 }
 
+// Checked builds: every read of a block (rows of 8 es-byte elements, the x
+// neighbours) lies inside a plane of `box` bytes.  Always true in release
+// builds.
+__device__ __forceinline__ bool offs_ok(const Offs &o, int box, int es, int *err)
+{
+    const int row = box - 8 * es + 1;
+    return check_range(err, o.r0, 0, row, kChkStreamSlot) &&
+           check_range(err, o.r1, 0, row, kChkStreamSlot) &&
+           check_range(err, o.dn, 0, row, kChkStreamSlot) &&
+           check_range(err, o.up, 0, row, kChkStreamSlot) &&
+           check_range(err, o.xl0, 0, box - es + 1, kChkStreamSlot) &&
+           check_range(err, o.xl1, 0, box - es + 1, kChkStreamSlot) &&
+           check_range(err, o.xr0, 0, box - es + 1, kChkStreamSlot) &&
+           check_range(err, o.xr1, 0, box - es + 1, kChkStreamSlot);
+}
+
+// A block that is read in place of one whose offsets failed offs_ok: the
+// start of the plane's third row (16-byte aligned), its results unused.
+__device__ __forceinline__ Offs safe_offs(int pitch_b)
+{
+    const int a = 2 * pitch_b;
+    return Offs{a, a, a, a, a, a, a, a};
+}
+
 // The two rows of a block at ring entry r, as packed pairs, clamped at the
 // cube's x faces (positions before a and from b on take the nearest inside
 // value) when the block straddles one.
@@ -310,11 +334,20 @@ __global__ void __maxnreg__(kWide2MaxRegs)
             const int zlo1 = max(w.z0 - 1, 0), zhi1 = min(w.z1, nz - 1);
             const int zlo0 = max(zlo1 - 1, 0), zhi0 = min(zhi1 + 1, nz - 1);
             const int x = w.x0 - 4 + 8 * kq, ya = w.y0 - 1 + 2 * jr;
-            const Offs o = block_offs(x, ya, nx, ny, w.x0 - 8, w.y0 - 2, IN_W * IS::ES, IS::ES);
+            Offs o = block_offs(x, ya, nx, ny, w.x0 - 8, w.y0 - 2, IN_W * IS::ES, IS::ES);
             const int a = max(0, -x), b = min(8, nx - x);
             const bool clamp = (a > 0 || b < 8) && a < b;
             const Kp k = make_kp<C>(kc);
             const int p1off = (2 * jr * P1_W + 8 * kq) * 4;  // the block in a stage-1 plane
+            // checked builds: reads inside the input box, both stores inside
+            // the stage-1 plane (else a safe block is read and nothing stored)
+            bool store_on = has_block;
+            if (!(offs_ok(o, IN_W * IN_H * IS::ES, IS::ES, err) &&
+                  check_range(err, p1off, 0, P1_W * P1_H * 4 - P1_W * 4 - 32 + 1,
+                              kChkStreamSlot))) {
+                o = safe_offs(IN_W * IS::ES);
+                store_on = false;
+            }
             const uint32_t kbase = kk;
             uint32_t r = kbase + static_cast<uint32_t>(zlo1 - zlo0);
             f2_t c0[4], c1[4], fb0[4], fb1[4];
@@ -348,7 +381,7 @@ __global__ void __maxnreg__(kWide2MaxRegs)
             return;                                                                            \
         if (p == zlo1 && t1 == 0)                                                              \
             p1_tile[k1 & (NP1 - 1)] = t;                                                       \
-        sts8x2(const_cast<unsigned char *>(p1.slot(k1)) + p1off, P1_W * 4, o0, o1, has_block); \
+        sts8x2(const_cast<unsigned char *>(p1.slot(k1)) + p1off, P1_W * 4, o0, o1, store_on);  \
         p1.arrive_full(k1);                                                                    \
         ++k1;                                                                                  \
         ++r;                                                                                   \
@@ -382,14 +415,17 @@ __global__ void __maxnreg__(kWide2MaxRegs)
         const Tile2 w = decode2(t, tiles_x, txy, lv);
         const int zlo1 = max(w.z0 - 1, 0), zhi1 = min(w.z1, nz - 1);
         const int x = w.x0 + 8 * q, ya = w.y0 + 2 * rp, yb = ya + 1;
-        const Offs o = block_offs(x, ya, nx, ny, w.x0 - 4, w.y0 - 1, P1_W * 4, 4);
+        Offs o = block_offs(x, ya, nx, ny, w.x0 - 4, w.y0 - 1, P1_W * 4, 4);
+        const bool p1_ok = offs_ok(o, P1_W * P1_H * 4, 4, err);  // checked builds
+        if (!p1_ok)
+            o = safe_offs(P1_W * 4);
         const Kp k = make_kp<C>(kc);
         const bool tile_ok = check_range(err, w.z1, w.z0 + 1, static_cast<int64_t>(nz) + 1,
                                          kChkStreamTile) &&
                              check_range(err, w.x0, 0, nx, kChkStreamTile) &&
                              check_range(err, w.y0, 0, ny, kChkStreamTile);
-        const bool act0 = tile_ok && x < nx && ya < ny;
-        const bool act1 = tile_ok && x < nx && yb < ny;
+        const bool act0 = tile_ok && p1_ok && x < nx && ya < ny;
+        const bool act1 = tile_ok && p1_ok && x < nx && yb < ny;
         typename Store<SO>::T *po = out + (static_cast<int64_t>(w.z0) * ny + ya) * nx + x;
         const uint32_t kb2 = k2;
         uint32_t r = kb2 + static_cast<uint32_t>(w.z0 - zlo1);
