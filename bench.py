@@ -276,14 +276,11 @@ class Issue:
 
 def pass_bytes(storage: str, T: int) -> float:
     """HBM bytes per voxel-iteration of afd_filter_ex at depth T (the
-    default kernels): one read and one write of the stored cube per pass at
-    depths 1 and 2; from depth 4 on, a chain of T/2 two-iteration launches
-    whose intermediate cubes are float32 (storage -> float32 -> ... ->
-    storage)."""
+    default kernels): one read and one write of the stored cube at depth 1;
+    from depth 2 on, a chain of T one-iteration launches whose intermediate
+    cubes are float32 (storage -> float32 -> ... -> storage)."""
     b = 4.0 if storage == "f32" else 2.0
-    if T <= 2:
-        return 2.0 * b / T
-    return (2.0 * b + 8.0 * (T // 2 - 1)) / T
+    return (2.0 * b + 8.0 * (T - 1)) / T
 
 
 def ceilings(storage: str, T: int, value: float, peak_gbs: float):
@@ -410,7 +407,7 @@ def line_precision(afd, ctx, cube, d_in, ref32, sig):
             "bf16: the one nearest the noise rms; i16: the finest whose range, 32 x scale, holds "
             "the cube's largest |I|); "
             "t_block iterations between roundings to the storage format (afd_filter_ex; "
-            "depths 4 and 8 as chains of two-iteration launches with float32 intermediate "
+            "depths 2, 4 and 8 as chains of one-iteration launches with float32 intermediate "
             "cubes); err_vs_oracle: against the FP64 oracle on the float32 input over four 16x32x32 boxes %s (oracle through the "
             "domain of dependence, exact; %.1f s of oracle), in units of sigma (faint: |I| < 3 "
             "sigma); gate_pass: rms and faint max both <= 1e-3 sigma; err_vs_f32: against the "

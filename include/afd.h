@@ -79,8 +79,10 @@ typedef enum {
 typedef enum {
     AFD_KERNEL_AUTO = 0,   /* streaming kernel when the layout allows it   */
     AFD_KERNEL_SIMPLE = 1, /* one voxel per thread, any layout             */
-    AFD_KERNEL_STREAM = 2  /* TMA-staged x-y tiles streamed along z;
+    AFD_KERNEL_STREAM = 2, /* TMA-staged x-y tiles streamed along z;
                               needs nx % 4 == 0 and a 16-byte aligned cube */
+    AFD_KERNEL_TWO_STAGE = 3 /* as AUTO, but afd_filter_ex's deep passes run
+                                on the two-iteration kernel */
 } afd_kernel;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -102,8 +104,9 @@ afd_status afd_set_stream(afd_ctx *ctx, void *cuda_stream);
  * AFD_EINVAL.  For afd_filter_ex's depth-1 passes on 2-byte storage, AUTO
  * runs the 8 x 2-voxel-per-thread streaming kernel and STREAM the 4 x 2 one;
  * for its passes of depth 2, 4 and 8 (nx a multiple of 8), AUTO runs chains
- * of the two-stage 8 x 2 kernel and STREAM the general temporally blocked
- * one.  All kernels give bit-identical results. */
+ * of one-iteration launches (storage -> float32 -> ... -> storage),
+ * TWO_STAGE chains of the two-iteration 8 x 2 kernel, and STREAM the general
+ * temporally blocked kernel.  All kernels give bit-identical results. */
 afd_status afd_set_kernel(afd_ctx *ctx, afd_kernel kernel);
 
 /* Tuning knob of the streaming kernel: the largest number of z planes one
@@ -266,16 +269,17 @@ afd_status afd_dequantize(afd_ctx *ctx, const void *in, float *out, int64_t n,
  * of depth 4, 2, 1 (at most T).  A pass is bit-identical to dequantise ->
  * that many afd_filter iterations -> quantise; with AFD_F32 the whole call
  * is bit-identical to afd_filter_out.  How a pass runs (afd_set_kernel):
- * under AUTO, with nx a multiple of 8, a pass of depth T >= 2 is T/2
- * launches of a two-iteration kernel whose intermediate cubes are float32
- * (storage -> float32 -> ... -> storage: (2 b + 8 (T/2 - 1)) / T bytes per
- * voxel-iteration for b-byte elements, e.g. 3 at depth 4 in 2 bytes; on
- * GB300 these bytes cost less than the instructions of a deeper fused pass);
- * under AFD_KERNEL_STREAM, or otherwise, one launch of the general blocked
- * kernel (2 b / T bytes).  Uses one cube of context scratch in the
- * storage format, plus two float32 cubes for passes of depth 4 or 8 under
- * AUTO, or when nx * element size is not a multiple of 16 bytes or K = +inf
- * (passes through float32 scratch).  Asynchronous. */
+ * under AUTO, with nx a multiple of 8, a pass of depth T >= 2 is T
+ * one-iteration launches whose intermediate cubes are float32 (storage ->
+ * float32 -> ... -> storage: (2 b + 8 (T - 1)) / T bytes per voxel-iteration
+ * for b-byte elements, e.g. 6 at depth 2 in 2 bytes; on GB300 these bytes
+ * cost less than the instructions of a fused pass); under
+ * AFD_KERNEL_TWO_STAGE, T/2 two-iteration launches ((2 b + 8 (T/2 - 1)) / T
+ * bytes); under AFD_KERNEL_STREAM, or otherwise, one launch of the general
+ * blocked kernel (2 b / T bytes).  Uses one cube of context scratch in the
+ * storage format, plus two float32 cubes for passes of depth 2 or more under
+ * AUTO and TWO_STAGE, or when nx * element size is not a multiple of 16
+ * bytes or K = +inf (passes through float32 scratch).  Asynchronous. */
 afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage storage,
                          float scale, int64_t nx, int64_t ny, int64_t nz,
                          const float *spacing, float K, float dt, int n_iter,

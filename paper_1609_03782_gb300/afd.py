@@ -23,7 +23,7 @@ LIB_PATH = os.environ.get("AFD_LIB", LIB_PATH)
 AFD_OK, AFD_EINVAL, AFD_ENOMEM, AFD_ECUDA, AFD_ETIMEOUT, AFD_EBUSY = range(6)
 COND = {"exponential": 0, "rational": 1}
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2, "i16": 3}
-KERNEL = {"auto": 0, "simple": 1, "stream": 2}
+KERNEL = {"auto": 0, "simple": 1, "stream": 2, "two_stage": 3}
 
 
 class AfdError(RuntimeError):

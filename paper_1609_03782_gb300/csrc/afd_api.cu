@@ -24,6 +24,7 @@
 #include "afd_internal.h"
 #include "afd_store.cuh"
 
+
 namespace afd_host {
 
 // ---- fault injection: AFD_FAULT=alloc:N makes the N-th scratch allocation
@@ -246,7 +247,7 @@ afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int
         if (!fits)
             return AFD_EINVAL;
         use_stream = true;
-    } else if (ctx->kernel == AFD_KERNEL_AUTO) {
+    } else if (ctx->kernel == AFD_KERNEL_AUTO || ctx->kernel == AFD_KERNEL_TWO_STAGE) {
         use_stream = fits;
     }
     if (kdev && !use_stream)
@@ -515,7 +516,7 @@ afd_status afd_set_stream(afd_ctx *ctx, void *cuda_stream)
 afd_status afd_set_kernel(afd_ctx *ctx, afd_kernel kernel)
 {
     if (!ctx || (kernel != AFD_KERNEL_AUTO && kernel != AFD_KERNEL_SIMPLE &&
-                 kernel != AFD_KERNEL_STREAM))
+                 kernel != AFD_KERNEL_STREAM && kernel != AFD_KERNEL_TWO_STAGE))
         return AFD_EINVAL;
     ctx->kernel = kernel;
     return AFD_OK;
@@ -1336,8 +1337,80 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
             if (e != cudaSuccess)
                 return cuda_fail(ctx, e);
         } else if (fits && T >= 2 && nx % 8 == 0 && ctx->kernel != AFD_KERNEL_STREAM &&
+                   ctx->kernel != AFD_KERNEL_TWO_STAGE &&
                    (kind == afd::COND_EXP || kind == afd::COND_RAT)) {
-            // depth T >= 2: T/2 launches of the two-stage 8 x 2-voxel kernel,
+            // depth T >= 2: T one-iteration launches, storage -> float32 ->
+            // ... -> float32 -> storage (the ends on the 8 x 2-voxel kernel,
+            // float32 -> float32 on the streaming kernel): dequantise, T
+            // float32 iterations, quantise, as one blocked pass of depth T
+            if (ctx->wide_bps == 0 || ctx->stream_bps == 0) {
+                e = afd::pm_wide_prepare();
+                if (e == cudaSuccess)
+                    e = afd::pm_wide_occupancy(&ctx->wide_bps);
+                if (e == cudaSuccess)
+                    e = afd::pm_stream_prepare();
+                if (e == cudaSuccess)
+                    e = afd::pm_stream_occupancy(&ctx->stream_bps);
+                if (e != cudaSuccess)
+                    return cuda_fail(ctx, e);
+                ctx->wide_bps = ctx->wide_bps < 1 ? 1 : ctx->wide_bps;
+                ctx->stream_bps = ctx->stream_bps < 1 ? 1 : ctx->stream_bps;
+            }
+            const size_t fbytes = static_cast<size_t>(n) * sizeof(float);
+            st = ensure_buffer(ctx, &ctx->chain_f32, &ctx->chain_f32_bytes, 2 * fbytes);
+            if (st != AFD_OK)
+                return st;
+            float *link_buf[2] = {ctx->chain_f32, ctx->chain_f32 + n};
+            for (int l = 0; l < T; ++l) {
+                const int s_in = l == 0 ? S : afd::STORE_F32;
+                const int s_out = l == T - 1 ? S : afd::STORE_F32;
+                const void *lsrc = l == 0 ? src_of(i) : link_buf[(l - 1) & 1];
+                void *ldst = l == T - 1 ? dst_of(i) : link_buf[l & 1];
+                const bool stream_link = s_in == afd::STORE_F32 && s_out == afd::STORE_F32;
+                int bw = 0, bh = 0, hx = 0;
+                if (stream_link)
+                    afd::pm_stream_box(afd::STORE_F32, &bw, &bh, &hx);
+                else
+                    afd::pm_wide_box(s_in, &bw, &bh);
+                CUtensorMap map;
+                st = encode_box_map(ctx, &map, lsrc, s_in, bw, bh, static_cast<int>(nx),
+                                    static_cast<int>(ny), static_cast<int>(nz));
+                if (st != AFD_OK)
+                    return st;
+                afd::StreamPlan plan =
+                    stream_link
+                        ? afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
+                                              static_cast<int>(nz), ctx->sm_count,
+                                              ctx->stream_bps, ctx->zc_hint)
+                        : afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
+                                              static_cast<int>(nz), ctx->sm_count, ctx->wide_bps,
+                                              ctx->zc_hint, afd::kWideTX, afd::kWideTY);
+                plan.pdl = prev_stream;
+                prev_stream = true;
+                if (!tiles_zeroed) {
+                    e = tiles_reset(ctx);
+                    tiles_zeroed = true;
+                }
+                if (e == cudaSuccess)
+                    e = stream_link
+                            ? afd::launch_pm_stream_s(afd::STORE_F32, kind, map, ldst,
+                                                      static_cast<int>(nx), static_cast<int>(ny),
+                                                      static_cast<int>(nz), k, plan,
+                                                      ctx->d_tiles, ctx->tiles_base, ctx->d_err,
+                                                      ctx->stream)
+                            : afd::launch_pm_wide_chain_end(
+                                  s_in, s_out, kind, map, ldst, static_cast<int>(nx),
+                                  static_cast<int>(ny), static_cast<int>(nz), k, plan,
+                                  ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream);
+                ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
+                ctx->launches++;
+                if (e != cudaSuccess)
+                    return cuda_fail(ctx, e);
+            }
+        } else if (fits && T >= 2 && nx % 8 == 0 && ctx->kernel == AFD_KERNEL_TWO_STAGE &&
+                   (kind == afd::COND_EXP || kind == afd::COND_RAT)) {
+            // depth T >= 2 (AFD_KERNEL_TWO_STAGE): T/2 launches of the
+            // two-stage 8 x 2-voxel kernel,
             // storage -> float32 -> ... -> float32 -> storage: dequantise, T
             // float32 iterations, quantise, as one blocked pass of depth T
             if (ctx->wide2_bps == 0) {

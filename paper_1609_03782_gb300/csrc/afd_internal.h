@@ -171,6 +171,14 @@ cudaError_t pm_wide_occupancy(int *blocks_per_sm);
 cudaError_t launch_pm_wide(int S, int cond, const CUtensorMap &tmap_in, void *out, int nx, int ny,
                            int nz, const Coef &k, const StreamPlan &plan, unsigned long long *ctr,
                            unsigned long long base, int *err, cudaStream_t stream);
+// The ends of a chain of one-iteration passes: a 2-byte cube in, float32
+// out (S 2-byte, SO = STORE_F32), or float32 in, 2-byte out (S = STORE_F32);
+// exponential or rational conductance.  The TMA map is over the input, with
+// pm_wide_box(S, ...).
+cudaError_t launch_pm_wide_chain_end(int S, int SO, int cond, const CUtensorMap &tmap_in,
+                                     void *out, int nx, int ny, int nz, const Coef &k,
+                                     const StreamPlan &plan, unsigned long long *ctr,
+                                     unsigned long long base, int *err, cudaStream_t stream);
 
 // ---- two iterations per pass, 8 x 2 voxels per thread (pm_wide2.cu) ---------
 // afd_filter_ex's passes of depth 2 and more: input format S, output format

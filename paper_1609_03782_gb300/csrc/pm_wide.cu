@@ -105,10 +105,10 @@ struct Dst {
 // z's slot is released, the z fluxes and the update computed and the block's
 // results stored.  In: plane z (c0, c1) and its lower z-face flux (fb0, fb1).
 // Out: plane z+1 (n0, n1) and the flux between them (fa0, fa1).
-template <int S, int C>
+template <int S, int SO, int C>
 __device__ __forceinline__ bool plane_step(const Ring<S> &ring, const Offs &o, const Kp &k,
                                            uint32_t r, bool has_next, int clamp_m,
-                                           const Dst<S> &d, const f2_t (&c0)[4],
+                                           const Dst<SO> &d, const f2_t (&c0)[4],
                                            const f2_t (&c1)[4], const f2_t (&fb0)[4],
                                            const f2_t (&fb1)[4], f2_t (&n0)[4], f2_t (&n1)[4],
                                            f2_t (&fa0)[4], f2_t (&fa1)[4])
@@ -146,9 +146,9 @@ __device__ __forceinline__ bool plane_step(const Ring<S> &ring, const Offs &o, c
         o0[i] = f2_add(c0[i], f2_add(s0[i], f2_sub(fa0[i], fb0[i])));
         o1[i] = f2_add(c1[i], f2_add(s1[i], f2_sub(fa1[i], fb1[i])));
     }
-    stg8<S>(d.po, o0,
-            d.act0 && check_range(ring.err, d.po - d.obase, 0, d.oext - 7, kChkStreamStore));
-    stg8<S>(d.po + d.px, o1,
+    stg8<SO>(d.po, o0,
+             d.act0 && check_range(ring.err, d.po - d.obase, 0, d.oext - 7, kChkStreamStore));
+    stg8<SO>(d.po + d.px, o1,
             d.act1 &&
                 check_range(ring.err, d.po + d.px - d.obase, 0, d.oext - 7, kChkStreamStore));
     return true;
@@ -162,7 +162,7 @@ struct WTile {
     int tx, ty, nq, rp;  // interior; 8-voxel blocks per row pair; row pairs
     int64_t px;          // row pitch of the cube (elements)
     const void *map;     // TMA map of the source, box (tx + 2 HX) x (ty + 2)
-    typename Store<S>::T *out;
+    void *out;           // the result, in the kernel's output format
     Coef k;
 };
 
@@ -172,7 +172,7 @@ template <int S>
 struct WOne {
     static constexpr bool kRagged = false;  // nx is a multiple of 8
     const void *map;
-    typename Store<S>::T *out;
+    void *out;
     int nx, ny, nz, tiles_x, txy;
     const ZLevels *lv;
     unsigned long long *ctr;
@@ -244,7 +244,7 @@ struct WMany {
             dr = rr.y;
         }
         w.map = &d.mapw[sr];
-        w.out = static_cast<typename Store<S>::T *>(d.buf[dr]);
+        w.out = d.buf[dr];
         w.k = d.coef;
     }
     __device__ __forceinline__ int64_t next(int64_t t) const
@@ -256,10 +256,11 @@ struct WMany {
     }
 };
 
-template <int S, int C, class Src>
+template <int S, int SO, int C, class Src>
 __device__ __forceinline__ void wide_body(const Src &src, int64_t ntiles, int *err)
 {
     typedef Ring_<S> G;
+    typedef typename Store<SO>::T EO;
     typedef typename Store<S>::T E;
     extern __shared__ unsigned char smem_raw[];
     const uint32_t sbase = smem_u32(smem_raw);
@@ -379,11 +380,11 @@ __device__ __forceinline__ void wide_body(const Src &src, int64_t ntiles, int *e
         // a block across the cube's x face: m < 8 of its voxels inside
         const int clamp_m = (Src::kRagged && x < nx && x + 8 > nx) ? nx - x : 0;
         const Kp k = make_kp<C>(w.k);
-        Dst<S> d;
+        Dst<SO> d;
         d.px = static_cast<int>(w.px);
         d.plane = w.px * ny;
-        d.po = w.out + (static_cast<int64_t>(w.z0) * ny + ya) * w.px + x;
-        d.obase = w.out;
+        d.po = static_cast<EO *>(w.out) + (static_cast<int64_t>(w.z0) * ny + ya) * w.px + x;
+        d.obase = static_cast<const EO *>(w.out);
         d.oext = static_cast<int64_t>(nz) * d.plane;
         d.act0 = lane_on && slot_ok && tile_ok && x < nx && ya < ny;
         d.act1 = lane_on && slot_ok && tile_ok && x < nx && yb < ny;
@@ -446,17 +447,17 @@ __device__ __forceinline__ void wide_body(const Src &src, int64_t ntiles, int *e
         f2_t n0[4], n1[4], fa0[4], fa1[4];
         int z = w.z0;
         for (; z + 1 < w.z1; z += 2, r += 2) {
-            if (!plane_step<S, C>(ring, o, k, r, z + 1 < nz, clamp_m, d, c0, c1, fb0, fb1, n0,
+            if (!plane_step<S, SO, C>(ring, o, k, r, z + 1 < nz, clamp_m, d, c0, c1, fb0, fb1, n0,
                                   n1, fa0, fa1))
                 return;
             d.po += d.plane;
-            if (!plane_step<S, C>(ring, o, k, r + 1, z + 2 < nz, clamp_m, d, n0, n1, fa0, fa1,
+            if (!plane_step<S, SO, C>(ring, o, k, r + 1, z + 2 < nz, clamp_m, d, n0, n1, fa0, fa1,
                                   c0, c1, fb0, fb1))
                 return;
             d.po += d.plane;
         }
         if (z < w.z1) {
-            if (!plane_step<S, C>(ring, o, k, r, z + 1 < nz, clamp_m, d, c0, c1, fb0, fb1, n0,
+            if (!plane_step<S, SO, C>(ring, o, k, r, z + 1 < nz, clamp_m, d, c0, c1, fb0, fb1, n0,
                                   n1, fa0, fa1))
                 return;
             ++r;
@@ -467,15 +468,17 @@ __device__ __forceinline__ void wide_body(const Src &src, int64_t ntiles, int *e
     }
 }
 
-template <int S, int C>
+// One cube, input format S, output format SO.
+template <int S, int SO, int C>
 __global__ void __maxnreg__(kWideMaxRegs)
-    pm_step_wide(const __grid_constant__ CUtensorMap tmap, typename Store<S>::T *__restrict__ out,
-                 int nx, int ny, int nz, int tiles_x, int txy, const __grid_constant__ ZLevels lv,
-                 int ntiles, unsigned long long *ctr, unsigned long long base, Coef kc, int *err)
+    pm_step_wide(const __grid_constant__ CUtensorMap tmap,
+                 typename Store<SO>::T *__restrict__ out, int nx, int ny, int nz, int tiles_x,
+                 int txy, const __grid_constant__ ZLevels lv, int ntiles,
+                 unsigned long long *ctr, unsigned long long base, Coef kc, int *err)
 {
     grid_dep_launch_dependents();  // the next pass may take SMs as this one frees them
     const WOne<S> src{&tmap, out, nx, ny, nz, tiles_x, txy, &lv, ctr, base, kc};
-    wide_body<S, C>(src, ntiles, err);
+    wide_body<S, SO, C>(src, ntiles, err);
 }
 
 template <int S, int C>
@@ -486,7 +489,7 @@ __global__ void __maxnreg__(kWideMaxRegs)
 {
     grid_dep_launch_dependents();
     const WMany<S> src{desc, list, roles, src_role, dst_role, ctr, base};
-    wide_body<S, C>(src, ntiles, err);
+    wide_body<S, S, C>(src, ntiles, err);
 }
 
 template <int S>
@@ -500,13 +503,27 @@ size_t smem_of()
 template <int S, int C>
 cudaError_t wide_attr()
 {
-    cudaError_t e = cudaFuncSetAttribute(pm_step_wide<S, C>,
+    cudaError_t e = cudaFuncSetAttribute(pm_step_wide<S, S, C>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem_of<S>()));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(pm_step_wide_batch<S, C>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(smem_of<S>()));
+    return e;
+}
+
+// storage -> float32 and float32 -> storage (the ends of a chain of
+// one-iteration passes), for the two conductances
+template <int S, int SO>
+cudaError_t wide_attr_pair()
+{
+    const int smem = static_cast<int>(smem_of<S>());
+    cudaError_t e = cudaFuncSetAttribute(pm_step_wide<S, SO, COND_EXP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(pm_step_wide<S, SO, COND_RAT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
 }
 
@@ -518,6 +535,12 @@ cudaError_t wide_attr_all()
         e = wide_attr<S, COND_RAT>();
     if (e == cudaSuccess)
         e = wide_attr<S, COND_LIN>();
+    if constexpr (S != STORE_F32) {
+        if (e == cudaSuccess)
+            e = wide_attr_pair<S, STORE_F32>();
+        if (e == cudaSuccess)
+            e = wide_attr_pair<STORE_F32, S>();
+    }
     return e;
 }
 
@@ -536,7 +559,7 @@ cudaLaunchConfig_t wide_cfg(int grid, size_t smem, bool pdl, cudaStream_t stream
     return cfg;
 }
 
-template <int S, int C>
+template <int S, int SO, int C>
 cudaError_t wide_launch(const CUtensorMap &tmap, void *out, int nx, int ny, int nz,
                         const Coef &k, const StreamPlan &plan, unsigned long long *ctr,
                         unsigned long long base, int *err, cudaStream_t stream)
@@ -545,8 +568,8 @@ cudaError_t wide_launch(const CUtensorMap &tmap, void *out, int nx, int ny, int 
         return cudaErrorInvalidValue;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = wide_cfg(plan.grid, smem_of<S>(), plan.pdl, stream, attr);
-    return cudaLaunchKernelEx(&cfg, pm_step_wide<S, C>, tmap,
-                              static_cast<typename Store<S>::T *>(out), nx, ny, nz, plan.tiles_x,
+    return cudaLaunchKernelEx(&cfg, pm_step_wide<S, SO, C>, tmap,
+                              static_cast<typename Store<SO>::T *>(out), nx, ny, nz, plan.tiles_x,
                               plan.tiles_x * plan.tiles_y, plan.lv, static_cast<int>(plan.ntiles),
                               ctr, base, k, err);
 }
@@ -558,11 +581,32 @@ cudaError_t wide_launch_c(int cond, const CUtensorMap &tmap, void *out, int nx, 
 {
     switch (cond) {
     case COND_EXP:
-        return wide_launch<S, COND_EXP>(tmap, out, nx, ny, nz, k, plan, ctr, base, err, stream);
+        return wide_launch<S, S, COND_EXP>(tmap, out, nx, ny, nz, k, plan, ctr, base, err,
+                                           stream);
     case COND_RAT:
-        return wide_launch<S, COND_RAT>(tmap, out, nx, ny, nz, k, plan, ctr, base, err, stream);
+        return wide_launch<S, S, COND_RAT>(tmap, out, nx, ny, nz, k, plan, ctr, base, err,
+                                           stream);
     default:
-        return wide_launch<S, COND_LIN>(tmap, out, nx, ny, nz, k, plan, ctr, base, err, stream);
+        return wide_launch<S, S, COND_LIN>(tmap, out, nx, ny, nz, k, plan, ctr, base, err,
+                                           stream);
+    }
+}
+
+template <int S, int SO>
+cudaError_t wide_launch_pair(int cond, const CUtensorMap &tmap, void *out, int nx, int ny,
+                             int nz, const Coef &k, const StreamPlan &plan,
+                             unsigned long long *ctr, unsigned long long base, int *err,
+                             cudaStream_t stream)
+{
+    switch (cond) {
+    case COND_EXP:
+        return wide_launch<S, SO, COND_EXP>(tmap, out, nx, ny, nz, k, plan, ctr, base, err,
+                                            stream);
+    case COND_RAT:
+        return wide_launch<S, SO, COND_RAT>(tmap, out, nx, ny, nz, k, plan, ctr, base, err,
+                                            stream);
+    default:
+        return cudaErrorInvalidValue;  // the chain's ends take the two conductances only
     }
 }
 
@@ -637,7 +681,7 @@ cudaError_t pm_wide_occupancy(int *blocks_per_sm)
 {
     int a = 0, b = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &a, pm_step_wide<STORE_F16, COND_RAT>, kWideThreads, smem_of<STORE_F16>());
+        &a, pm_step_wide<STORE_F16, STORE_F16, COND_RAT>, kWideThreads, smem_of<STORE_F16>());
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &b, pm_step_wide_batch<STORE_F32, COND_RAT>, kWideThreads, smem_of<STORE_F32>());
@@ -663,6 +707,39 @@ cudaError_t launch_pm_wide(int S, int cond, const CUtensorMap &tmap_in, void *ou
         return wide_launch_c<STORE_F32>(cond, tmap_in, out, nx, ny, nz, k, plan, ctr, base, err,
                                         stream);
     }
+}
+
+cudaError_t launch_pm_wide_chain_end(int S, int SO, int cond, const CUtensorMap &tmap_in,
+                                     void *out, int nx, int ny, int nz, const Coef &k,
+                                     const StreamPlan &plan, unsigned long long *ctr,
+                                     unsigned long long base, int *err, cudaStream_t stream)
+{
+    if (S == STORE_F32) {
+        switch (SO) {
+        case STORE_F16:
+            return wide_launch_pair<STORE_F32, STORE_F16>(cond, tmap_in, out, nx, ny, nz, k, plan,
+                                                          ctr, base, err, stream);
+        case STORE_BF16:
+            return wide_launch_pair<STORE_F32, STORE_BF16>(cond, tmap_in, out, nx, ny, nz, k,
+                                                           plan, ctr, base, err, stream);
+        case STORE_I16:
+            return wide_launch_pair<STORE_F32, STORE_I16>(cond, tmap_in, out, nx, ny, nz, k, plan,
+                                                          ctr, base, err, stream);
+        }
+    } else if (SO == STORE_F32) {
+        switch (S) {
+        case STORE_F16:
+            return wide_launch_pair<STORE_F16, STORE_F32>(cond, tmap_in, out, nx, ny, nz, k, plan,
+                                                          ctr, base, err, stream);
+        case STORE_BF16:
+            return wide_launch_pair<STORE_BF16, STORE_F32>(cond, tmap_in, out, nx, ny, nz, k,
+                                                           plan, ctr, base, err, stream);
+        case STORE_I16:
+            return wide_launch_pair<STORE_I16, STORE_F32>(cond, tmap_in, out, nx, ny, nz, k, plan,
+                                                          ctr, base, err, stream);
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_pm_wide_batch(int S, int cond, const BatchDesc *desc, const int2 *list,

@@ -27,7 +27,7 @@ def test_ceilings_pick_the_lower_bound(monkeypatch):
     assert f16["bound"] == "issue"
     assert f16["issue_ceiling"] == pytest.approx(152 * 4 * 32 * 2.07e9 / 30.86 / 1e9)
     t4 = bench.ceilings("i16", 4, 418.0, 6786.2)
-    assert t4["hbm_ceiling"] == pytest.approx(6786.2 / 3.0)   # 3 bytes per voxel-iteration
+    assert t4["hbm_ceiling"] == pytest.approx(6786.2 / 7.0)   # 7 bytes per voxel-iteration
     assert t4["bound"] == "issue"
     unknown = bench.ceilings("f16", 8, 100.0, 6786.2)  # no instruction count recorded
     assert unknown["issue_ceiling"] is None and unknown["bound"] == "hbm"
@@ -97,10 +97,10 @@ def test_i16_scale_is_the_finest_that_holds_the_range():
 
 def test_pass_bytes():
     assert bench.pass_bytes("f32", 1) == 8.0 and bench.pass_bytes("f16", 1) == 4.0
-    assert bench.pass_bytes("f16", 2) == 2.0
-    assert bench.pass_bytes("f16", 4) == 3.0      # 2 + 4 | 4 + 2 bytes over 4 iterations
-    assert bench.pass_bytes("i16", 8) == 3.5      # 2 + 4 | 4 + 4 | 4 + 4 | 4 + 2 over 8
-    assert bench.pass_bytes("f32", 4) == 4.0
+    assert bench.pass_bytes("f16", 2) == 6.0      # 2 + 4 | 4 + 2 bytes over 2 iterations
+    assert bench.pass_bytes("f16", 4) == 7.0      # 2 + 4 | 4 + 4 | 4 + 4 | 4 + 2 over 4
+    assert bench.pass_bytes("i16", 8) == 7.5
+    assert bench.pass_bytes("f32", 4) == 8.0
 
 
 def test_pow2_near():

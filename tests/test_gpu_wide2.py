@@ -1,11 +1,12 @@
-"""afd_filter_ex's passes of depth 2, 4 and 8 on the two-iteration kernel
-(pm_wide2.cu: two stages of 8 x 2-voxel blocks; depth T as T/2 launches with
-float32 intermediate cubes; the default for widths that are a multiple of 8)
-against the general temporally blocked kernel of the same depth
-(afd_set_kernel 'stream'), bit for bit, for every storage format: both
-compute dequantise -> T canonical float32 iterations -> quantise, so any
-difference is a staging, halo, boundary, hand-over or chaining mistake.  With
-float32 storage a pass also equals single-iteration passes.  Shapes cover
+"""afd_filter_ex's passes of depth 2, 4 and 8 three ways, bit for bit, for
+every storage format: chains of T one-iteration launches with float32
+intermediate cubes (the default for widths that are a multiple of 8; the
+ends on pm_wide.cu's storage <-> float32 kernels), chains of T/2 launches of
+the two-iteration kernel (pm_wide2.cu, afd_set_kernel 'two_stage'), and the
+general temporally blocked kernel (afd_set_kernel 'stream').  All compute
+dequantise -> T canonical float32 iterations -> quantise, so any difference
+is a staging, halo, boundary, hand-over or chaining mistake.  With float32
+storage a pass also equals single-iteration passes.  Shapes cover
 single planes, rows and columns, widths and heights at and around the
 128 x 28 tile, iteration counts with a remainder (shallower passes at the
 end), both conductances with anisotropic spacing, int16 with a non-unit
@@ -73,9 +74,10 @@ def test_depth_equals_blocked_kernel(afd, ctx, shape, storage, T):
     src = stored(cube(shape, sum(shape) + len(storage) + T), storage)
     for cond, sp, K, dt in CASES:
         for n in (T, 2 * T - 1):
-            a = run(afd, ctx, src, storage, K, dt, n, cond, sp, "auto", t_block=T)
             b = run(afd, ctx, src, storage, K, dt, n, cond, sp, "stream", t_block=T)
-            assert np.array_equal(a, b), (cond, n, int((a != b).sum()))
+            for kern in ("auto", "two_stage"):
+                a = run(afd, ctx, src, storage, K, dt, n, cond, sp, kern, t_block=T)
+                assert np.array_equal(a, b), (kern, cond, n, int((a != b).sum()))
 
 
 @pytest.mark.parametrize("T", [2, 4, 8])
@@ -83,9 +85,10 @@ def test_depth_equals_blocked_kernel(afd, ctx, shape, storage, T):
 def test_float32_depth_equals_single_passes(afd, ctx, shape, T):
     src = stored(cube(shape, 3 * sum(shape)), "f32")
     for cond, sp, K, dt in CASES:
-        a = run(afd, ctx, src, "f32", K, dt, 2 * T, cond, sp, "auto", t_block=T)
         b = run(afd, ctx, src, "f32", K, dt, 2 * T, cond, sp, "stream", t_block=1)
-        assert np.array_equal(a, b), (cond, T)
+        for kern in ("auto", "two_stage"):
+            a = run(afd, ctx, src, "f32", K, dt, 2 * T, cond, sp, kern, t_block=T)
+            assert np.array_equal(a, b), (kern, cond, T)
 
 
 @pytest.mark.parametrize("T", [2, 4])
@@ -94,19 +97,21 @@ def test_float32_depth_equals_single_passes(afd, ctx, shape, T):
 def test_depth_zchunks_and_in_place(afd, ctx, zc, storage, T):
     src = stored(cube((23, 45, 200), zc), storage)
     ref = run(afd, ctx, src, storage, 1.0, 1 / 8, 2 * T, "rational", None, "stream", t_block=T)
-    got = run(afd, ctx, src, storage, 1.0, 1 / 8, 2 * T, "rational", None, "auto", t_block=T,
-              zc=zc)
-    assert np.array_equal(got, ref)
-    got = run(afd, ctx, src, storage, 1.0, 1 / 8, 2 * T, "rational", None, "auto", t_block=T,
-              zc=zc, inplace=True)
-    assert np.array_equal(got, ref)
+    for kern in ("auto", "two_stage"):
+        got = run(afd, ctx, src, storage, 1.0, 1 / 8, 2 * T, "rational", None, kern,
+                  t_block=T, zc=zc)
+        assert np.array_equal(got, ref), kern
+        got = run(afd, ctx, src, storage, 1.0, 1 / 8, 2 * T, "rational", None, kern,
+                  t_block=T, zc=zc, inplace=True)
+        assert np.array_equal(got, ref), kern
 
 
 @pytest.mark.parametrize("T", [2, 4, 8])
 def test_depth_against_oracle(afd, ctx, T):
     c = cube((20, 37, 136), 5)
-    got = run(afd, ctx, stored(c, "f32"), "f32", 1.0, 0.125, 10, "rational", None, "auto",
-              t_block=T)
     ref = oracle.pm_filter(c, 1.0, 0.125, 10, "rational")
-    # float32 rounding of 10 iterations over values up to 9 (the bright voxel)
-    assert np.abs(got.view(np.float32) - ref).max() <= 4e-4
+    for kern in ("auto", "two_stage"):
+        got = run(afd, ctx, stored(c, "f32"), "f32", 1.0, 0.125, 10, "rational", None, kern,
+                  t_block=T)
+        # float32 rounding of 10 iterations over values up to 9 (the bright voxel)
+        assert np.abs(got.view(np.float32) - ref).max() <= 4e-4, kern
