@@ -1171,6 +1171,182 @@ afd_status afd_dequantize(afd_ctx *ctx, const void *in, float *out, int64_t n,
     return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
 }
 
+namespace {
+// One afd_filter_ex call's launches: programmatic dependent launches chain
+// the streaming kernels, and the tile counter is reset once per call.
+struct ExLaunch {
+    afd_ctx *ctx;
+    int kind;
+    afd::Coef k;
+    int nx, ny, nz;
+    bool prev_stream = false;  // the previous launch was a streaming-kernel launch
+    bool tiles_zeroed = false;
+};
+
+// Plan bookkeeping shared by the streaming launches: PDL after a streaming
+// launch, the tile counter's reset, and its base for the next launch.
+cudaError_t ex_stream_begin(ExLaunch &L, afd::StreamPlan &plan)
+{
+    plan.pdl = L.prev_stream;
+    L.prev_stream = true;
+    cudaError_t e = cudaSuccess;
+    if (!L.tiles_zeroed) {
+        e = tiles_reset(L.ctx);
+        L.tiles_zeroed = true;
+    }
+    return e;
+}
+
+afd_status ex_stream_end(ExLaunch &L, const afd::StreamPlan &plan, cudaError_t e)
+{
+    L.ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
+    L.ctx->launches++;
+    return e == cudaSuccess ? AFD_OK : cuda_fail(L.ctx, e);
+}
+
+// One iteration on the 8 x 2-voxel kernel, format s_in to s_out (equal, or
+// one of them float32: the ends of a chain).
+afd_status ex_wide(ExLaunch &L, int s_in, int s_out, const void *src, void *dst)
+{
+    afd_ctx *ctx = L.ctx;
+    if (ctx->wide_bps == 0) {
+        cudaError_t e = afd::pm_wide_prepare();
+        if (e == cudaSuccess)
+            e = afd::pm_wide_occupancy(&ctx->wide_bps);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e);
+        if (ctx->wide_bps < 1)
+            ctx->wide_bps = 1;
+    }
+    int bw = 0, bh = 0;
+    afd::pm_wide_box(s_in, &bw, &bh);
+    CUtensorMap map;
+    const afd_status st = encode_box_map(ctx, &map, src, s_in, bw, bh, L.nx, L.ny, L.nz);
+    if (st != AFD_OK)
+        return st;
+    afd::StreamPlan plan = afd::pm_stream_plan(L.nx, L.ny, L.nz, ctx->sm_count, ctx->wide_bps,
+                                               ctx->zc_hint, afd::kWideTX, afd::kWideTY);
+    cudaError_t e = ex_stream_begin(L, plan);
+    if (e == cudaSuccess)
+        e = s_in == s_out
+                ? afd::launch_pm_wide(s_in, L.kind, map, dst, L.nx, L.ny, L.nz, L.k, plan,
+                                      ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream)
+                : afd::launch_pm_wide_chain_end(s_in, s_out, L.kind, map, dst, L.nx, L.ny, L.nz,
+                                                L.k, plan, ctx->d_tiles, ctx->tiles_base,
+                                                ctx->d_err, ctx->stream);
+    return ex_stream_end(L, plan, e);
+}
+
+// One iteration on the barrier-free 4 x 2-voxel streaming kernel, on the
+// stored format.
+afd_status ex_stream(ExLaunch &L, int S, const void *src, void *dst)
+{
+    afd_ctx *ctx = L.ctx;
+    if (ctx->stream_bps == 0) {
+        cudaError_t e = afd::pm_stream_prepare();
+        if (e == cudaSuccess)
+            e = afd::pm_stream_occupancy(&ctx->stream_bps);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e);
+        if (ctx->stream_bps < 1)
+            ctx->stream_bps = 1;
+    }
+    int bw = 0, bh = 0, hx = 0;
+    afd::pm_stream_box(S, &bw, &bh, &hx);
+    CUtensorMap map;
+    const afd_status st = encode_box_map(ctx, &map, src, S, bw, bh, L.nx, L.ny, L.nz);
+    if (st != AFD_OK)
+        return st;
+    afd::StreamPlan plan = afd::pm_stream_plan(L.nx, L.ny, L.nz, ctx->sm_count, ctx->stream_bps,
+                                               ctx->zc_hint);
+    cudaError_t e = ex_stream_begin(L, plan);
+    if (e == cudaSuccess)
+        e = afd::launch_pm_stream_s(S, L.kind, map, dst, L.nx, L.ny, L.nz, L.k, plan,
+                                    ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream);
+    return ex_stream_end(L, plan, e);
+}
+
+// Two iterations on the two-stage kernel, format s_in to s_out.
+afd_status ex_wide2(ExLaunch &L, int s_in, int s_out, const void *src, void *dst)
+{
+    afd_ctx *ctx = L.ctx;
+    if (ctx->wide2_bps == 0) {
+        cudaError_t e = afd::pm_wide2_prepare();
+        if (e == cudaSuccess)
+            e = afd::pm_wide2_occupancy(&ctx->wide2_bps);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e);
+        if (ctx->wide2_bps < 1)
+            ctx->wide2_bps = 1;
+    }
+    int bw = 0, bh = 0;
+    afd::pm_wide2_box(&bw, &bh);
+    CUtensorMap map;
+    const afd_status st = encode_box_map(ctx, &map, src, s_in, bw, bh, L.nx, L.ny, L.nz);
+    if (st != AFD_OK)
+        return st;
+    afd::StreamPlan plan = afd::pm_stream_plan(L.nx, L.ny, L.nz, ctx->sm_count, ctx->wide2_bps,
+                                               ctx->zc_hint, afd::kWide2TX, afd::kWide2TY);
+    cudaError_t e = ex_stream_begin(L, plan);
+    if (e == cudaSuccess)
+        e = afd::launch_pm_wide2(s_in, s_out, L.kind, map, dst, L.nx, L.ny, L.nz, L.k, plan,
+                                 ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream);
+    return ex_stream_end(L, plan, e);
+}
+
+// A pass of depth T >= 2 as a chain through two float32 context cubes,
+// storage -> float32 -> ... -> float32 -> storage: dequantise, T float32
+// iterations, quantise, the result of one blocked pass of depth T.  Links
+// of one iteration (the ends on the 8 x 2-voxel kernel, float32 -> float32
+// on the streaming kernel), or of two on the two-stage kernel (two_stage).
+afd_status ex_chain(ExLaunch &L, int S, int T, bool two_stage, int64_t n, const void *src,
+                    void *dst)
+{
+    afd_ctx *ctx = L.ctx;
+    afd_status st = ensure_buffer(ctx, &ctx->chain_f32, &ctx->chain_f32_bytes,
+                                  2 * static_cast<size_t>(n) * sizeof(float));
+    if (st != AFD_OK)
+        return st;
+    float *link_buf[2] = {ctx->chain_f32, ctx->chain_f32 + n};
+    const int links = two_stage ? T / 2 : T;
+    for (int l = 0; l < links && st == AFD_OK; ++l) {
+        const int s_in = l == 0 ? S : afd::STORE_F32;
+        const int s_out = l == links - 1 ? S : afd::STORE_F32;
+        const void *lsrc = l == 0 ? src : link_buf[(l - 1) & 1];
+        void *ldst = l == links - 1 ? dst : link_buf[l & 1];
+        if (two_stage)
+            st = ex_wide2(L, s_in, s_out, lsrc, ldst);
+        else if (s_in == afd::STORE_F32 && s_out == afd::STORE_F32)
+            st = ex_stream(L, afd::STORE_F32, lsrc, ldst);
+        else
+            st = ex_wide(L, s_in, s_out, lsrc, ldst);
+    }
+    return st;
+}
+
+// One pass of depth T on the general temporally blocked kernel.
+afd_status ex_blocked(ExLaunch &L, int S, int T, const void *src, void *dst)
+{
+    afd_ctx *ctx = L.ctx;
+    if (!ctx->tb_ready[S][T]) {
+        const cudaError_t e = afd::tb_prepare(S, T);
+        if (e != cudaSuccess)
+            return cuda_fail(ctx, e);
+        ctx->tb_ready[S][T] = true;
+    }
+    CUtensorMap map;
+    const afd_status st = encode_tb_map(ctx, &map, src, S, T, L.nx, L.ny, L.nz);
+    if (st != AFD_OK)
+        return st;
+    const afd::TbPlan plan = afd::tb_plan(S, T, L.nx, L.ny, L.nz, ctx->sm_count, ctx->zc_hint);
+    const cudaError_t e = afd::tb_launch(S, T, L.kind, map, dst, L.nx, L.ny, L.nz, L.k, plan,
+                                         ctx->d_err, ctx->stream);
+    L.prev_stream = false;
+    ctx->launches++;
+    return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
+}
+}  // namespace
+
 afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage storage,
                          float scale, int64_t nx, int64_t ny, int64_t nz, const float *spacing,
                          float K, float dt, int n_iter, afd_conductance cond, int t_block)
@@ -1258,241 +1434,27 @@ afd_status afd_filter_ex(afd_ctx *ctx, const void *in, void *out, afd_storage st
     const bool fits = ((nx * es) % 16 == 0) && (reinterpret_cast<uintptr_t>(in) & 15u) == 0 &&
                       (reinterpret_cast<uintptr_t>(out) & 15u) == 0 && !std::isinf(K) &&
                       (reinterpret_cast<uintptr_t>(scr) & 15u) == 0;
-    bool tiles_zeroed = false;
-    bool prev_stream = false;  // the previous pass was a streaming-kernel launch
+    ExLaunch L{ctx, kind, k, static_cast<int>(nx), static_cast<int>(ny), static_cast<int>(nz)};
+    // deep passes on the fast routes: exponential or rational g, nx a multiple of 8
+    const bool deep_ok = fits && nx % 8 == 0 && (kind == afd::COND_EXP || kind == afd::COND_RAT);
     for (int i = 0; i < npass; ++i) {
         const afd_host::TraceRange pass_trace("pass");
         const int T = depth_of(i);
         if (fits && T == 1 && S != afd::STORE_F32 && ctx->kernel != AFD_KERNEL_STREAM) {
-            // depth 1 on 2-byte storage: the 8 x 2-voxel streaming kernel
-            if (ctx->wide_bps == 0) {
-                e = afd::pm_wide_prepare();
-                if (e == cudaSuccess)
-                    e = afd::pm_wide_occupancy(&ctx->wide_bps);
-                if (e != cudaSuccess)
-                    return cuda_fail(ctx, e);
-                if (ctx->wide_bps < 1)
-                    ctx->wide_bps = 1;
-            }
-            int bw = 0, bh = 0;
-            afd::pm_wide_box(S, &bw, &bh);
-            CUtensorMap map;
-            st = encode_box_map(ctx, &map, src_of(i), S, bw, bh, static_cast<int>(nx),
-                                static_cast<int>(ny), static_cast<int>(nz));
-            if (st != AFD_OK)
-                return st;
-            afd::StreamPlan plan =
-                afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
-                                    static_cast<int>(nz), ctx->sm_count, ctx->wide_bps,
-                                    ctx->zc_hint, afd::kWideTX, afd::kWideTY);
-            plan.pdl = prev_stream;
-            prev_stream = true;
-            if (!tiles_zeroed) {
-                e = tiles_reset(ctx);
-                tiles_zeroed = true;
-            }
-            if (e == cudaSuccess)
-                e = afd::launch_pm_wide(S, kind, map, dst_of(i), static_cast<int>(nx),
-                                        static_cast<int>(ny), static_cast<int>(nz), k, plan,
-                                        ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream);
-            ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
-            ctx->launches++;
-            if (e != cudaSuccess)
-                return cuda_fail(ctx, e);
+            st = ex_wide(L, S, S, src_of(i), dst_of(i));   // the 8 x 2-voxel kernel
         } else if (fits && T == 1) {
-            // depth 1: the barrier-free streaming kernel, on the stored format
-            if (ctx->stream_bps == 0) {
-                e = afd::pm_stream_prepare();
-                if (e == cudaSuccess)
-                    e = afd::pm_stream_occupancy(&ctx->stream_bps);
-                if (e != cudaSuccess)
-                    return cuda_fail(ctx, e);
-                if (ctx->stream_bps < 1)
-                    ctx->stream_bps = 1;
-            }
-            int bw = 0, bh = 0, hx = 0;
-            afd::pm_stream_box(S, &bw, &bh, &hx);
-            CUtensorMap map;
-            st = encode_box_map(ctx, &map, src_of(i), S, bw, bh, static_cast<int>(nx),
-                                static_cast<int>(ny), static_cast<int>(nz));
-            if (st != AFD_OK)
-                return st;
-            afd::StreamPlan plan =
-                afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
-                                    static_cast<int>(nz), ctx->sm_count, ctx->stream_bps,
-                                    ctx->zc_hint);
-            plan.pdl = prev_stream;
-            prev_stream = true;
-            if (!tiles_zeroed) {
-                e = tiles_reset(ctx);
-                tiles_zeroed = true;
-            }
-            if (e == cudaSuccess)
-                e = afd::launch_pm_stream_s(S, kind, map, dst_of(i), static_cast<int>(nx),
-                                            static_cast<int>(ny), static_cast<int>(nz), k, plan,
-                                            ctx->d_tiles, ctx->tiles_base, ctx->d_err,
-                                            ctx->stream);
-            ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
-            ctx->launches++;
-            if (e != cudaSuccess)
-                return cuda_fail(ctx, e);
-        } else if (fits && T >= 2 && nx % 8 == 0 && ctx->kernel != AFD_KERNEL_STREAM &&
-                   ctx->kernel != AFD_KERNEL_TWO_STAGE &&
-                   (kind == afd::COND_EXP || kind == afd::COND_RAT)) {
-            // depth T >= 2: T one-iteration launches, storage -> float32 ->
-            // ... -> float32 -> storage (the ends on the 8 x 2-voxel kernel,
-            // float32 -> float32 on the streaming kernel): dequantise, T
-            // float32 iterations, quantise, as one blocked pass of depth T
-            if (ctx->wide_bps == 0 || ctx->stream_bps == 0) {
-                e = afd::pm_wide_prepare();
-                if (e == cudaSuccess)
-                    e = afd::pm_wide_occupancy(&ctx->wide_bps);
-                if (e == cudaSuccess)
-                    e = afd::pm_stream_prepare();
-                if (e == cudaSuccess)
-                    e = afd::pm_stream_occupancy(&ctx->stream_bps);
-                if (e != cudaSuccess)
-                    return cuda_fail(ctx, e);
-                ctx->wide_bps = ctx->wide_bps < 1 ? 1 : ctx->wide_bps;
-                ctx->stream_bps = ctx->stream_bps < 1 ? 1 : ctx->stream_bps;
-            }
-            const size_t fbytes = static_cast<size_t>(n) * sizeof(float);
-            st = ensure_buffer(ctx, &ctx->chain_f32, &ctx->chain_f32_bytes, 2 * fbytes);
-            if (st != AFD_OK)
-                return st;
-            float *link_buf[2] = {ctx->chain_f32, ctx->chain_f32 + n};
-            for (int l = 0; l < T; ++l) {
-                const int s_in = l == 0 ? S : afd::STORE_F32;
-                const int s_out = l == T - 1 ? S : afd::STORE_F32;
-                const void *lsrc = l == 0 ? src_of(i) : link_buf[(l - 1) & 1];
-                void *ldst = l == T - 1 ? dst_of(i) : link_buf[l & 1];
-                const bool stream_link = s_in == afd::STORE_F32 && s_out == afd::STORE_F32;
-                int bw = 0, bh = 0, hx = 0;
-                if (stream_link)
-                    afd::pm_stream_box(afd::STORE_F32, &bw, &bh, &hx);
-                else
-                    afd::pm_wide_box(s_in, &bw, &bh);
-                CUtensorMap map;
-                st = encode_box_map(ctx, &map, lsrc, s_in, bw, bh, static_cast<int>(nx),
-                                    static_cast<int>(ny), static_cast<int>(nz));
-                if (st != AFD_OK)
-                    return st;
-                afd::StreamPlan plan =
-                    stream_link
-                        ? afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
-                                              static_cast<int>(nz), ctx->sm_count,
-                                              ctx->stream_bps, ctx->zc_hint)
-                        : afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
-                                              static_cast<int>(nz), ctx->sm_count, ctx->wide_bps,
-                                              ctx->zc_hint, afd::kWideTX, afd::kWideTY);
-                plan.pdl = prev_stream;
-                prev_stream = true;
-                if (!tiles_zeroed) {
-                    e = tiles_reset(ctx);
-                    tiles_zeroed = true;
-                }
-                if (e == cudaSuccess)
-                    e = stream_link
-                            ? afd::launch_pm_stream_s(afd::STORE_F32, kind, map, ldst,
-                                                      static_cast<int>(nx), static_cast<int>(ny),
-                                                      static_cast<int>(nz), k, plan,
-                                                      ctx->d_tiles, ctx->tiles_base, ctx->d_err,
-                                                      ctx->stream)
-                            : afd::launch_pm_wide_chain_end(
-                                  s_in, s_out, kind, map, ldst, static_cast<int>(nx),
-                                  static_cast<int>(ny), static_cast<int>(nz), k, plan,
-                                  ctx->d_tiles, ctx->tiles_base, ctx->d_err, ctx->stream);
-                ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
-                ctx->launches++;
-                if (e != cudaSuccess)
-                    return cuda_fail(ctx, e);
-            }
-        } else if (fits && T >= 2 && nx % 8 == 0 && ctx->kernel == AFD_KERNEL_TWO_STAGE &&
-                   (kind == afd::COND_EXP || kind == afd::COND_RAT)) {
-            // depth T >= 2 (AFD_KERNEL_TWO_STAGE): T/2 launches of the
-            // two-stage 8 x 2-voxel kernel,
-            // storage -> float32 -> ... -> float32 -> storage: dequantise, T
-            // float32 iterations, quantise, as one blocked pass of depth T
-            if (ctx->wide2_bps == 0) {
-                e = afd::pm_wide2_prepare();
-                if (e == cudaSuccess)
-                    e = afd::pm_wide2_occupancy(&ctx->wide2_bps);
-                if (e != cudaSuccess)
-                    return cuda_fail(ctx, e);
-                if (ctx->wide2_bps < 1)
-                    ctx->wide2_bps = 1;
-            }
-            const int links = T / 2;
-            float *link_buf[2] = {nullptr, nullptr};
-            if (links > 1) {
-                const size_t fbytes = static_cast<size_t>(n) * sizeof(float);
-                st = ensure_buffer(ctx, &ctx->chain_f32, &ctx->chain_f32_bytes, 2 * fbytes);
-                if (st != AFD_OK)
-                    return st;
-                link_buf[0] = ctx->chain_f32;
-                link_buf[1] = ctx->chain_f32 + n;
-            }
-            int bw = 0, bh = 0;
-            afd::pm_wide2_box(&bw, &bh);
-            const afd::StreamPlan plan0 =
-                afd::pm_stream_plan(static_cast<int>(nx), static_cast<int>(ny),
-                                    static_cast<int>(nz), ctx->sm_count, ctx->wide2_bps,
-                                    ctx->zc_hint, afd::kWide2TX, afd::kWide2TY);
-            for (int l = 0; l < links; ++l) {
-                const int s_in = l == 0 ? S : afd::STORE_F32;
-                const int s_out = l == links - 1 ? S : afd::STORE_F32;
-                const void *lsrc = l == 0 ? src_of(i) : link_buf[(l - 1) & 1];
-                void *ldst = l == links - 1 ? dst_of(i) : link_buf[l & 1];
-                CUtensorMap map;
-                st = encode_box_map(ctx, &map, lsrc, s_in, bw, bh, static_cast<int>(nx),
-                                    static_cast<int>(ny), static_cast<int>(nz));
-                if (st != AFD_OK)
-                    return st;
-                afd::StreamPlan plan = plan0;
-                plan.pdl = prev_stream;
-                prev_stream = true;
-                if (!tiles_zeroed) {
-                    e = tiles_reset(ctx);
-                    tiles_zeroed = true;
-                }
-                if (e == cudaSuccess)
-                    e = afd::launch_pm_wide2(s_in, s_out, kind, map, ldst, static_cast<int>(nx),
-                                             static_cast<int>(ny), static_cast<int>(nz), k, plan,
-                                             ctx->d_tiles, ctx->tiles_base, ctx->d_err,
-                                             ctx->stream);
-                ctx->tiles_base += static_cast<unsigned long long>(plan.ntiles);
-                ctx->launches++;
-                if (e != cudaSuccess)
-                    return cuda_fail(ctx, e);
-            }
+            st = ex_stream(L, S, src_of(i), dst_of(i));    // the 4 x 2-voxel kernel
+        } else if (deep_ok && T >= 2 && ctx->kernel != AFD_KERNEL_STREAM) {
+            st = ex_chain(L, S, T, ctx->kernel == AFD_KERNEL_TWO_STAGE, n, src_of(i), dst_of(i));
         } else if (fits) {
-            if (!ctx->tb_ready[S][T]) {
-                e = afd::tb_prepare(S, T);
-                if (e != cudaSuccess)
-                    return cuda_fail(ctx, e);
-                ctx->tb_ready[S][T] = true;
-            }
-            CUtensorMap map;
-            st = encode_tb_map(ctx, &map, src_of(i), S, T, static_cast<int>(nx),
-                               static_cast<int>(ny), static_cast<int>(nz));
-            if (st != AFD_OK)
-                return st;
-            const afd::TbPlan plan = afd::tb_plan(S, T, static_cast<int>(nx), static_cast<int>(ny),
-                                                  static_cast<int>(nz), ctx->sm_count, ctx->zc_hint);
-            e = afd::tb_launch(S, T, kind, map, dst_of(i), static_cast<int>(nx),
-                               static_cast<int>(ny), static_cast<int>(nz), k, plan, ctx->d_err,
-                               ctx->stream);
-            prev_stream = false;
-            ctx->launches++;
-            if (e != cudaSuccess)
-                return cuda_fail(ctx, e);
+            st = ex_blocked(L, S, T, src_of(i), dst_of(i));
         } else {
             st = fallback_pass(ctx, S, units, src_of(i), dst_of(i), nx, ny, nz, spacing, K, dt, T,
                                cond);
-            prev_stream = false;
-            if (st != AFD_OK)
-                return st;
+            L.prev_stream = false;
         }
+        if (st != AFD_OK)
+            return st;
     }
     if (dst_of(npass - 1) != out) {
         e = cudaMemcpyAsync(out, dst_of(npass - 1), bytes, cudaMemcpyDeviceToDevice, ctx->stream);
