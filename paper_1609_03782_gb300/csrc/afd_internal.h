@@ -181,12 +181,12 @@ cudaError_t launch_pm_wide_chain_end(int S, int SO, int cond, const CUtensorMap 
                                      unsigned long long base, int *err, cudaStream_t stream);
 
 // ---- two iterations per pass, 8 x 2 voxels per thread (pm_wide2.cu) ---------
-// afd_filter_ex's passes of depth 2 and more: input format S, output format
-// SO, either equal or one of them float32 (a chain 2-byte -> float32 -> ...
-// -> 2-byte is one pass of depth 2 x links).  128 x kWide2TY output tiles; a
-// TMA box of 144 x (kWide2TY + 4) input elements around the tile (x starts
-// at x0 - 8, y at y0 - 2); nx a multiple of 8, 16-byte aligned pointers.
-// Plan: pm_stream_plan with these tiles.
+// afd_filter_ex's passes of depth 2 and more under AFD_KERNEL_TWO_STAGE:
+// input format S, output format SO, either equal or one of them float32 (a
+// chain 2-byte -> float32 -> ... -> 2-byte is one pass of depth 2 x links).
+// 128 x kWide2TY output tiles; a TMA box of 144 x (kWide2TY + 4) input
+// elements around the tile (x starts at x0 - 8, y at y0 - 2); nx a multiple
+// of 8, 16-byte aligned pointers.  Plan: pm_stream_plan with these tiles.
 #ifndef AFD_WIDE2_TY
 #define AFD_WIDE2_TY 28  // 8 stage-1 + 7 stage-2 + 1 producer warps: 16 x 32 x 128 registers
 #endif
