@@ -8,7 +8,10 @@ variant is bit-identical):
 * the tile shape of a resident batch (``afd_batch_set_tiles``): 64 x 32
   tiles of 4 x 2 voxels per thread, or per-cube tiles of 8 x 2 voxels per
   thread (tile columns of at most 128 voxels, as tall as the threads cover);
-* the temporal-blocking depth of ``afd_filter_ex`` (1, 2, 4 or 8).
+* the temporal-blocking depth of ``afd_filter_ex`` (1, 2, 4 or 8; at least
+  a caller's minimum, which bounds the roundings to 2-byte storage) and the
+  route its deeper passes take (``afd_set_kernel``: chains of one-iteration
+  launches or of the two-stage kernel).
 
 Results are cached in a JSON file keyed by what the choice depends on: the
 cube shape rounded to powers of two (or the batch's voxel count and cube
@@ -25,6 +28,8 @@ import threading
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "afd_tune.json")
 ZCHUNKS = (0, 8, 16, 32, 64)
 DEPTHS = (1, 2, 4, 8)
+# afd_filter_ex's routes for passes of depth 2 or more (afd_set_kernel names)
+ROUTES = ("auto", "two_stage")
 TILES = ("wide", "64x32")
 BATCH_ZCHUNKS = (64, 32, 16)
 
@@ -111,19 +116,33 @@ class Tuner:
 
     def tune_filter_ex(self, afd, ctx, src, dst, storage, scale, K, dt, n_iter,
                        conductance="rational", spacing=None, depths=DEPTHS,
-                       zchunks=(0, 16, 32)):
-        """Choose (t_block, z-chunk) for afd_filter_ex on this shape; the
-        z-chunk is left applied to the context, t_block is returned."""
-        key = shape_key("filter_ex", src.shape, storage, conductance, n_iter)
-        cands = [(t, z) for t in depths for z in zchunks]
+                       zchunks=(0, 16, 32), routes=ROUTES, min_depth=1):
+        """Choose (t_block, z-chunk, route) for afd_filter_ex on this shape:
+        the fastest with t_block >= min_depth.  A caller that wants at most
+        n_iter / d roundings to the storage format (the error of 2-byte
+        storage grows with them) sets min_depth = d.  `routes` are
+        afd_set_kernel names tried for passes of depth 2 or more (one-
+        iteration chains, two-stage chains); depth 1 takes the first.  The
+        z-chunk and route are left applied to the context; t_block is
+        returned."""
+        key = "%s|min depth %d" % (shape_key("filter_ex", src.shape, storage, conductance,
+                                             n_iter), min_depth)
+        cands = [(t, z, r) for t in depths if t >= min_depth for z in zchunks
+                 for r in (routes if t >= 2 else routes[:1])]
+        if not cands:
+            raise ValueError("no depth in %r is at least %d" % (tuple(depths), min_depth))
+
+        def apply(c):
+            afd.afd_set_stream_zchunk(ctx, c[1])
+            afd.afd_set_kernel(ctx, c[2])
 
         def run(c):
-            afd.afd_set_stream_zchunk(ctx, c[1])
+            apply(c)
             afd.afd_filter_ex(ctx, src, dst, storage, scale, K, dt, n_iter, conductance,
                               spacing, c[0])
 
         best = self.pick(key, cands, run)
-        afd.afd_set_stream_zchunk(ctx, best[1])
+        apply(best)
         return best[0]
 
 

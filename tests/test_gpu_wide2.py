@@ -115,3 +115,25 @@ def test_depth_against_oracle(afd, ctx, T):
                   t_block=T)
         # float32 rounding of 10 iterations over values up to 9 (the bright voxel)
         assert np.abs(got.view(np.float32) - ref).max() <= 4e-4, kern
+
+
+def test_tuner_picks_a_route_at_the_minimum_depth(afd, ctx):
+    """tune.Tuner.tune_filter_ex with min_depth 4 on a real cube: it times
+    depths 4 and 8 over both routes, leaves its choice applied, and the
+    tuned call gives the general kernel's bits."""
+    from paper_1609_03782_gb300 import tune
+    src = stored(cube((24, 64, 128), 11), "f16")
+    out = torch.empty_like(src)
+    t = tune.Tuner(cache_path=None, reps=1)
+    try:
+        T = t.tune_filter_ex(afd, ctx, src, out, "f16", 1.0, 1.0, 1 / 8, 8, "rational",
+                             zchunks=(0,), min_depth=4)
+        assert T in (4, 8)
+        afd.afd_filter_ex(ctx, src, out, "f16", 1.0, 1.0, 1 / 8, 8, "rational", None, T)
+        afd.afd_sync(ctx)
+        got = out.view(torch.int16).cpu().numpy().view(np.uint16)
+    finally:
+        afd.afd_set_kernel(ctx, "auto")
+        afd.afd_set_stream_zchunk(ctx, 0)
+    ref = run(afd, ctx, src, "f16", 1.0, 1 / 8, 8, "rational", None, "stream", t_block=T)
+    assert np.array_equal(got, ref)

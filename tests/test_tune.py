@@ -2,6 +2,8 @@
 caches the choice per key in JSON, and reuses it without timing again."""
 import json
 
+import pytest
+
 from paper_1609_03782_gb300 import tune
 
 
@@ -71,3 +73,44 @@ def test_tune_batch_picks_tile_kind_and_zchunk(tmp_path):
     ms = json.loads((tmp_path / "c.json").read_text())[tune.batch_key(B.shapes, "f32",
                                                                       "rational", 20)]["ms"]
     assert any("wide" in k for k in ms) and any("64x32" in k for k in ms)
+
+
+class _FakeEx:
+    """Records afd_filter_ex calls with the knobs applied (no GPU)."""
+
+    def __init__(self):
+        self.state, self.calls = {"zc": 0, "kernel": "auto"}, []
+
+    def afd_set_stream_zchunk(self, ctx, zc):
+        self.state["zc"] = zc
+
+    def afd_set_kernel(self, ctx, k):
+        self.state["kernel"] = k
+
+    def afd_filter_ex(self, ctx, src, dst, storage, scale, K, dt, n, cond, sp, t):
+        self.calls.append((t, self.state["zc"], self.state["kernel"]))
+
+
+def test_tune_filter_ex_respects_min_depth_and_applies_route(tmp_path):
+    class Src:
+        shape = (64, 256, 256)
+
+    fake = _FakeEx()
+    cost = {}
+    for t in tune.DEPTHS:
+        for z in (0, 16):
+            for r in tune.ROUTES:
+                cost[(t, z, r)] = 10.0 - t - (0.5 if r == "two_stage" else 0.0)
+    cost[(1, 0, "auto")] = 1.0                       # depth 1 fastest overall
+    t = tune.Tuner(str(tmp_path / "c.json"), timer=lambda fn, reps: (fn(), cost[fake.calls[-1]])[1])
+    assert t.tune_filter_ex(fake, None, Src(), None, "f16", 1.0, 1.0, 0.125, 20,
+                            zchunks=(0, 16)) == 1
+    # at least depth 4: the fastest of depths 4 and 8 over both routes
+    fake.calls.clear()
+    best = t.tune_filter_ex(fake, None, Src(), None, "f16", 1.0, 1.0, 0.125, 20,
+                            zchunks=(0, 16), min_depth=4)
+    assert best == 8 and fake.state == {"zc": 0, "kernel": "two_stage"}
+    assert all(c[0] >= 4 for c in fake.calls)
+    assert not any(c[0] == 1 and c[2] != "auto" for c in fake.calls)
+    with pytest.raises(ValueError):
+        t.tune_filter_ex(fake, None, Src(), None, "f16", 1.0, 1.0, 0.125, 20, min_depth=16)
