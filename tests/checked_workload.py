@@ -60,9 +60,20 @@ def main(path):
                 r = torch.empty_like(q)
                 afd.afd_filter_ex(ctx, q, r, st, 1.0, 1.1, 0.1, 6, "exponential", None, T)
                 step("ex_%s_%s_%d" % (shape, st, T), r)
+            # the deep passes' other route: chains of the two-stage kernel
+            afd.afd_set_kernel(ctx, "two_stage")
+            r = torch.empty_like(q)
+            afd.afd_filter_ex(ctx, q, r, st, 1.0, 1.1, 0.1, 6, "exponential", None, 4)
+            afd.afd_set_kernel(ctx, "auto")
+            step("ex2_%s_%s_4" % (shape, st), r)
         r = torch.empty_like(src)
         afd.afd_filter_ex(ctx, src, r, "f32", 1.0, 1.1, 0.1, 6, "rational", None, 2)
         step("ex_%s_f32_2" % (shape,), r)
+        afd.afd_set_kernel(ctx, "two_stage")
+        r = torch.empty_like(src)
+        afd.afd_filter_ex(ctx, src, r, "f32", 1.0, 1.1, 0.1, 6, "rational", None, 2)
+        afd.afd_set_kernel(ctx, "auto")
+        step("ex2_%s_f32_2" % (shape,), r)
     # a resident batch with odd widths, float32 and float16; a short service
     shapes = [(3, 5, 7), (40, 70, 129), (9, 20, 33), (17, 40, 196)]
     for storage, dt_ in (("f32", torch.float32), ("f16", torch.float16)):
