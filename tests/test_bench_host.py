@@ -74,7 +74,9 @@ def test_summary_is_short_and_last():
     line = {"value": 780.0, "roofline": {"frac": 0.94}, "e2e": {"value": 769.0},
             "cpu_openmp": {"value": 3.1, "cores": 16, "roofline": {"frac": 0.3}},
             "cpu_baseline": {"value": 0.06},
-            "lines": {"precision": {"rows": [row] * 13},
+            "lines": {"precision": {"rows": [row] * 13,
+                                    "best_gate_pass": {"storage": "i16", "t_block": 4,
+                                                       "value": 855.2, "speedup_vs_f32": 1.064}},
                       "batch": {"f32": {"value": 660.0}, "f16": {"value": 657.0}},
                       "serving": {"rates": [{"lambda_per_s": 50, "requests": 3000,
                                              "p50_ms": 1.3, "p99_ms": 3.8}] * 4,
@@ -82,6 +84,7 @@ def test_summary_is_short_and_last():
     s = bench.summary(line)
     assert len(json.dumps(s)) < 1400
     assert s["precision"][0] == ["f16", 1, 800.0, 1.02, 2e-5, 0.02, False]
+    assert s["precision_best_gate_pass"] == ["i16", 4, 855.0, 1.06]
     assert s["saturation_gvox_iter_per_s"] == 600.0
 
 
