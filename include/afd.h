@@ -232,6 +232,22 @@ afd_status afd_filter_slabs(afd_ctx *ctx, const float *host_in, float *host_out,
                             float dt, int n_iter, afd_conductance cond, int64_t slab_nz,
                             int halo);
 
+/* afd_filter_intensity for a cube in HOST memory, through the device in
+ * z-slabs as afd_filter_slabs: the paper's intensity-driven update (Sec.
+ * 3.3, after eq. "conductivepara") also reaches one plane per iteration, so
+ * the same ghost planes make the result bit-identical to
+ * afd_filter_intensity on the whole cube.  It is also the paper's own GPU
+ * protocol, the cube in from and out to RAM (Sec. 6), with the copies of one
+ * slab overlapping the passes of another.
+ *   host_in, host_out, host_tmp, slab_nz, halo   as afd_filter_slabs.
+ *   C, K, rms, tau, n_iter                        as afd_filter_intensity.
+ * Synchronous.  AFD_EINVAL for bad arguments (nothing is done), else as
+ * afd_sync. */
+afd_status afd_filter_intensity_slabs(afd_ctx *ctx, const float *host_in, float *host_out,
+                                      float *host_tmp, int64_t nx, int64_t ny, int64_t nz,
+                                      const float *C, float K, float rms, float tau, int n_iter,
+                                      int64_t slab_nz, int halo);
+
 /* Round a float32 cube into a 2-byte storage format (precision line): out[i]
  * = RN(in[i] / scale) in float16 or bfloat16, or RN(in[i] * 1024 / scale)
  * as int16 clamped to +-32767; nearest, ties to even.

@@ -66,6 +66,8 @@ def _load():
         "afd_pass_timing_read": ([vp, ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_int64)], c_int),
         "afd_filter_intensity": ([vp, vp, vp, i64, i64, i64, vp, f32, f32, f32, c_int], c_int),
+        "afd_filter_intensity_slabs": ([vp, vp, vp, vp, i64, i64, i64, vp, f32, f32, f32, c_int,
+                                        i64, c_int], c_int),
         "afd_selftest_wait": ([vp, i64], c_int),
         "afd_quantize": ([vp, vp, vp, i64, c_int, f32], c_int),
         "afd_dequantize": ([vp, vp, vp, i64, c_int, f32], c_int),
@@ -412,6 +414,30 @@ def afd_filter_slabs(ctx: Context, host_in: torch.Tensor, host_out: torch.Tensor
                                  float(K), float(dt), int(n_iter), COND[conductance],
                                  int(slab_nz), int(halo)),
            "afd_filter_slabs", ctx)
+    return host_out
+
+
+def afd_filter_intensity_slabs(ctx: Context, host_in: torch.Tensor, host_out: torch.Tensor,
+                               K: float, rms: float, tau: float, n_iter: int,
+                               C=(5.0, 5.0, 5.0), slab_nz: int = 64, halo: int = 8,
+                               host_tmp: torch.Tensor = None) -> torch.Tensor:
+    """The paper's intensity-driven filter on a float32 CPU cube, through the
+    device in z-slabs as afd_filter_slabs; synchronous.  Bit-identical to
+    afd_filter_intensity on the whole cube."""
+    for t in (host_in, host_out) + ((host_tmp,) if host_tmp is not None else ()):
+        if t.dtype != torch.float32 or t.is_cuda:
+            raise ValueError("afd_filter_intensity_slabs takes float32 CPU tensors")
+        if t.shape != host_in.shape:
+            raise ValueError("afd_filter_intensity_slabs: shapes differ")
+    p_in, nx, ny, nz = _cube_args(host_in)
+    p_out, _, _, _ = _cube_args(host_out)
+    p_tmp = _cube_args(host_tmp)[0] if host_tmp is not None else None
+    _use_current_stream(ctx)
+    c = (ctypes.c_float * 3)(*[float(v) for v in C])
+    _check(_lib.afd_filter_intensity_slabs(ctx.handle, p_in, p_out, p_tmp, nx, ny, nz, c,
+                                           float(K), float(rms), float(tau), int(n_iter),
+                                           int(slab_nz), int(halo)),
+           "afd_filter_intensity_slabs", ctx)
     return host_out
 
 

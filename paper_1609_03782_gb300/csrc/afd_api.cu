@@ -209,20 +209,67 @@ afd_status run_passes(afd_ctx *ctx, const float *in, float *out, int64_t nx, int
                       int64_t nz, int kind, const afd::Coef &k, int n_iter,
                       const afd::Coef *kdev = nullptr);
 
+// What a host-staged call filters with: a conductance kind and its
+// coefficients, or the identity.
+struct DeviceFilter {
+    int kind;
+    afd::Coef k;
+    bool identity;
+};
+
+// The per-face filter of afd_filter (K = 0: the identity).
+DeviceFilter per_face_filter(const float *spacing, float K, float dt, afd_conductance cond)
+{
+    DeviceFilter f{};
+    f.identity = K == 0.0f;
+    if (!f.identity)
+        f.k = afd::make_coef(spacing, K, dt, cond == AFD_COND_EXPONENTIAL, &f.kind);
+    return f;
+}
+
+// The intensity-driven filter of afd_filter_intensity (K = 0 or rms = 0:
+// the identity).
+DeviceFilter intensity_filter(const float *C, float K, float rms, float tau)
+{
+    DeviceFilter f{};
+    f.identity = K == 0.0f || rms == 0.0f;
+    f.kind = afd::COND_INT;
+    if (!f.identity)
+        f.k = afd::make_coef_intensity(C, K, rms, tau);
+    return f;
+}
+
+// The intensity form's parameters as afd_filter_intensity accepts them.
+bool intensity_args_ok(const float *C, float K, float rms, float tau, int n_iter)
+{
+    if (!C || n_iter < 0)
+        return false;
+    for (int a = 0; a < 3; ++a)
+        if (!(C[a] >= 0.0f) || !std::isfinite(C[a]))
+            return false;
+    return !(std::isnan(K) || K < 0.0f || std::isnan(rms) || rms < 0.0f || !(tau > 0.0f) ||
+             !std::isfinite(tau));
+}
+
 afd_status filter_device(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
-                         int64_t nz, const float *spacing, float K, float dt, int n_iter,
-                         afd_conductance cond)
+                         int64_t nz, const DeviceFilter &f, int n_iter)
 {
     const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
-    if (n_iter == 0 || K == 0.0f) {  // identity
+    if (n_iter == 0 || f.identity) {
         cudaError_t e = cudaSuccess;
         if (in != out)
             e = cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
         return e == cudaSuccess ? AFD_OK : cuda_fail(ctx, e);
     }
-    int kind = 0;
-    const afd::Coef k = afd::make_coef(spacing, K, dt, cond == AFD_COND_EXPONENTIAL, &kind);
-    return run_passes(ctx, in, out, nx, ny, nz, kind, k, n_iter);
+    return run_passes(ctx, in, out, nx, ny, nz, f.kind, f.k, n_iter);
+}
+
+afd_status filter_device(afd_ctx *ctx, const float *in, float *out, int64_t nx, int64_t ny,
+                         int64_t nz, const float *spacing, float K, float dt, int n_iter,
+                         afd_conductance cond)
+{
+    return filter_device(ctx, in, out, nx, ny, nz, per_face_filter(spacing, K, dt, cond),
+                         n_iter);
 }
 
 // n_iter >= 1 passes of conductance kind `kind` with coefficients k, or
@@ -909,13 +956,7 @@ afd_status afd_filter_intensity(afd_ctx *ctx, const float *in, float *out, int64
                                 float tau, int n_iter)
 {
     const afd_host::TraceRange trace_("afd_filter_intensity");
-    if (!ctx || !in || !out || !C || !dims_ok(nx, ny, nz) || n_iter < 0)
-        return AFD_EINVAL;
-    for (int a = 0; a < 3; ++a)
-        if (!(C[a] >= 0.0f) || !std::isfinite(C[a]))
-            return AFD_EINVAL;
-    if (std::isnan(K) || K < 0.0f || std::isnan(rms) || rms < 0.0f || !(tau > 0.0f) ||
-        !std::isfinite(tau))
+    if (!ctx || !in || !out || !dims_ok(nx, ny, nz) || !intensity_args_ok(C, K, rms, tau, n_iter))
         return AFD_EINVAL;
     if (in != out) {
         const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
@@ -994,9 +1035,8 @@ afd_status ensure_host_slot(afd_ctx *ctx, int slot, size_t bytes)
 // points at the destination of plane oz0).  Stream-ordered: the copies run on
 // the copy streams and overlap the other slot's work.
 afd_status enqueue_host_filter(afd_ctx *ctx, int slot, const float *host_in, float *host_out,
-                               int64_t nx, int64_t ny, int64_t nz, const float *spacing, float K,
-                               float dt, int n_iter, afd_conductance cond, int64_t oz0,
-                               int64_t oz1)
+                               int64_t nx, int64_t ny, int64_t nz, const DeviceFilter &f,
+                               int n_iter, int64_t oz0, int64_t oz1)
 {
     const size_t bytes = static_cast<size_t>(nx * ny * nz) * sizeof(float);
     afd_status st0 = ensure_host_slot(ctx, slot, bytes);
@@ -1018,7 +1058,7 @@ afd_status enqueue_host_filter(afd_ctx *ctx, int slot, const float *host_in, flo
         e = cudaStreamWaitEvent(ctx->stream, s.copied_out, 0);
     if (e != cudaSuccess)
         return cuda_fail(ctx, e);
-    afd_status st = filter_device(ctx, d_in, d_out, nx, ny, nz, spacing, K, dt, n_iter, cond);
+    afd_status st = filter_device(ctx, d_in, d_out, nx, ny, nz, f, n_iter);
     if (st != AFD_OK)
         return st;
     e = cudaEventRecord(s.filtered, ctx->stream);
@@ -1053,8 +1093,8 @@ afd_status afd_filter_host(afd_ctx *ctx, const float *host_in, float *host_out, 
     afd_status st = set_device(ctx);
     if (st != AFD_OK)
         return st;
-    st = enqueue_host_filter(ctx, 0, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter, cond,
-                             0, nz);
+    st = enqueue_host_filter(ctx, 0, host_in, host_out, nx, ny, nz,
+                             per_face_filter(spacing, K, dt, cond), n_iter, 0, nz);
     if (st != AFD_OK)
         return st;
     return afd_sync(ctx);
@@ -1071,21 +1111,21 @@ afd_status afd_filter_host_async(afd_ctx *ctx, const float *host_in, float *host
     if (st != AFD_OK)
         return st;
     const int slot = static_cast<int>(ctx->host_calls & 1ull);
-    st = enqueue_host_filter(ctx, slot, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter,
-                             cond, 0, nz);
+    st = enqueue_host_filter(ctx, slot, host_in, host_out, nx, ny, nz,
+                             per_face_filter(spacing, K, dt, cond), n_iter, 0, nz);
     if (st == AFD_OK)
         ctx->host_calls++;
     return st;
 }
 
-afd_status afd_filter_slabs(afd_ctx *ctx, const float *host_in, float *host_out, float *host_tmp,
-                            int64_t nx, int64_t ny, int64_t nz, const float *spacing, float K,
-                            float dt, int n_iter, afd_conductance cond, int64_t slab_nz, int halo)
+namespace {
+// The z-slab rounds of afd_filter_slabs and afd_filter_intensity_slabs, for
+// any filter whose iteration reaches one plane (arguments checked by the
+// callers).
+afd_status run_slabs(afd_ctx *ctx, const float *host_in, float *host_out, float *host_tmp,
+                     int64_t nx, int64_t ny, int64_t nz, const DeviceFilter &f, int n_iter,
+                     int64_t slab_nz, int halo)
 {
-    const afd_host::TraceRange trace_("afd_filter_slabs");
-    if (!host_args_ok(ctx, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter, cond) ||
-        slab_nz < 1 || halo < 1 || host_out == host_in)
-        return AFD_EINVAL;
     const int rounds = n_iter == 0 ? 1 : (n_iter + halo - 1) / halo;
     if (rounds > 1 && (!host_tmp || host_tmp == host_in || host_tmp == host_out))
         return AFD_EINVAL;
@@ -1120,7 +1160,7 @@ afd_status afd_filter_slabs(afd_ctx *ctx, const float *host_in, float *host_out,
             // are the true zero-flux faces) are the whole cube's
             const int64_t lo = std::max<int64_t>(0, z0 - its), hi = std::min(nz, z1 + its);
             st = enqueue_host_filter(ctx, k & 1, src + lo * plane, dst + z0 * plane, nx, ny,
-                                     hi - lo, spacing, K, dt, its, cond, z0 - lo, z1 - lo);
+                                     hi - lo, f, its, z0 - lo, z1 - lo);
         }
         // the next round reads what this round wrote: its copies in wait for
         // every copy out of this one (in order on the copy-out stream)
@@ -1137,6 +1177,33 @@ afd_status afd_filter_slabs(afd_ctx *ctx, const float *host_in, float *host_out,
         st = afd_sync(ctx);
     cudaEventDestroy(round_done);
     return st;
+}
+}  // namespace
+
+afd_status afd_filter_slabs(afd_ctx *ctx, const float *host_in, float *host_out, float *host_tmp,
+                            int64_t nx, int64_t ny, int64_t nz, const float *spacing, float K,
+                            float dt, int n_iter, afd_conductance cond, int64_t slab_nz, int halo)
+{
+    const afd_host::TraceRange trace_("afd_filter_slabs");
+    if (!host_args_ok(ctx, host_in, host_out, nx, ny, nz, spacing, K, dt, n_iter, cond) ||
+        slab_nz < 1 || halo < 1 || host_out == host_in)
+        return AFD_EINVAL;
+    return run_slabs(ctx, host_in, host_out, host_tmp, nx, ny, nz,
+                     per_face_filter(spacing, K, dt, cond), n_iter, slab_nz, halo);
+}
+
+afd_status afd_filter_intensity_slabs(afd_ctx *ctx, const float *host_in, float *host_out,
+                                      float *host_tmp, int64_t nx, int64_t ny, int64_t nz,
+                                      const float *C, float K, float rms, float tau, int n_iter,
+                                      int64_t slab_nz, int halo)
+{
+    const afd_host::TraceRange trace_("afd_filter_intensity_slabs");
+    if (!ctx || !host_in || !host_out || !dims_ok(nx, ny, nz) ||
+        !intensity_args_ok(C, K, rms, tau, n_iter) || slab_nz < 1 || halo < 1 ||
+        host_out == host_in)
+        return AFD_EINVAL;
+    return run_slabs(ctx, host_in, host_out, host_tmp, nx, ny, nz,
+                     intensity_filter(C, K, rms, tau), n_iter, slab_nz, halo);
 }
 
 afd_status afd_quantize(afd_ctx *ctx, const float *in, void *out, int64_t n, afd_storage storage,

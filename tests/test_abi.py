@@ -72,6 +72,10 @@ def test_host_side_rejections_need_no_gpu(libpath):
                                   (None, None, None, 4, 4, 4, None, 1.0, 0.1, 1, 1)),
         "afd_filter_slabs": ([vp, vp, vp, vp, i64, i64, i64, vp, f32, f32, ci, ci, i64, ci],
                              (None, None, None, None, 4, 4, 4, None, 1.0, 0.1, 1, 1, 2, 1)),
+        "afd_filter_intensity_slabs": ([vp, vp, vp, vp, i64, i64, i64, vp, f32, f32, f32, ci,
+                                        i64, ci],
+                                       (None, None, None, None, 4, 4, 4, None, 1.5, 1.0, 0.03,
+                                        2, 2, 1)),
         "afd_smooth_box": ([vp, vp, vp, i64, i64, i64, vp], (None, None, None, 4, 4, 4, None)),
         "afd_smooth_gauss": ([vp, vp, vp, i64, i64, i64, vp, vp, f32],
                              (None, None, None, 4, 4, 4, None, None, 3.0)),

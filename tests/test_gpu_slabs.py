@@ -107,3 +107,50 @@ def test_slab_decomposition_gpu_step_single_rank(afd, ctx):
     afd.afd_sync(ctx)
     ref = whole(afd, ctx, cube, 1.1, 0.1, 11, "rational")
     assert torch.equal(got.cpu().view(torch.int32), ref.view(torch.int32))
+
+
+# the paper's intensity-driven form through the same slabs
+@pytest.mark.parametrize("shape,slab_nz,halo,n", [
+    ((40, 33, 68), 8, 3, 10),
+    ((29, 17, 36), 5, 2, 7),
+    ((12, 20, 24), 1, 3, 6),
+    ((9, 35, 132), 4, 20, 6),
+    ((64, 24, 40), 16, 20, 20),    # the paper's n = 20 in one round
+])
+def test_intensity_slabs_equal_whole_cube(afd, ctx, shape, slab_nz, halo, n):
+    cube = synth.cutout(shape, 3 * sum(shape) + n)
+    C, K, tau = (5.0, 4.0, 3.0), 1.5, 0.0325
+    d = torch.from_numpy(cube).cuda()
+    rms = afd.afd_noise_rms(ctx, d)
+    o = torch.empty_like(d)
+    afd.afd_filter_intensity(ctx, d, o, K, rms, tau, n, C)
+    afd.afd_sync(ctx)
+    ref = o.cpu()
+    h_in = torch.from_numpy(cube).pin_memory()
+    h_out = torch.full(cube.shape, float("nan")).pin_memory()
+    h_tmp = torch.full(cube.shape, float("nan")).pin_memory()
+    afd.afd_filter_intensity_slabs(ctx, h_in, h_out, K, rms, tau, n, C, slab_nz, halo, h_tmp)
+    assert torch.equal(h_in, torch.from_numpy(cube))
+    assert torch.equal(h_out.view(torch.int32), ref.view(torch.int32))
+
+
+def test_intensity_slabs_identities_and_argument_checks(afd, ctx):
+    cube = synth.cutout((10, 12, 16), 5)
+    h_in = torch.from_numpy(cube)
+    h_out = torch.empty_like(h_in)
+    for K, rms, n in ((0.0, 1.0, 5), (1.5, 0.0, 5), (1.5, 1.0, 0)):   # S = 0 or no iterations
+        afd.afd_filter_intensity_slabs(ctx, h_in, h_out, K, rms, 0.0325, n, (5.0, 5.0, 5.0), 4, 2,
+                                       torch.empty_like(h_in))
+        assert torch.equal(h_out, h_in)
+    bad = [dict(tau=0.0), dict(tau=-1.0), dict(K=-1.0), dict(C=(1.0, -1.0, 1.0)),
+           dict(slab_nz=0), dict(halo=0)]
+    for b in bad:
+        kw = dict(K=1.5, rms=1.0, tau=0.0325, n_iter=3, C=(5.0, 5.0, 5.0), slab_nz=4, halo=2)
+        kw.update(b)
+        with pytest.raises(afd.AfdError):
+            afd.afd_filter_intensity_slabs(ctx, h_in, h_out, host_tmp=torch.empty_like(h_in),
+                                           **kw)
+    with pytest.raises(afd.AfdError):           # the result may not overwrite the input
+        afd.afd_filter_intensity_slabs(ctx, h_in, h_in, 1.5, 1.0, 0.0325, 3)
+    with pytest.raises(afd.AfdError):           # several rounds need host_tmp
+        afd.afd_filter_intensity_slabs(ctx, h_in, h_out, 1.5, 1.0, 0.0325, 5, slab_nz=4, halo=2)
